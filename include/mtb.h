@@ -1,0 +1,169 @@
+/*
+ * mtb.h -- C ABI of the GB300 median-threshold-bitmap (MTB) alignment library.
+ *
+ * The library aligns the exposures of an HDR stack by a global integer
+ * translation, following Ward's MTB method as Alpay, Aydemir & Temizel,
+ * "Accelerating Translational Image Registration for HDR Images on GPU"
+ * (arXiv 2007.06483), describe it:
+ *   Sec. III-A  gray conversion, per-level histogram and median, the threshold
+ *               bitmap (pixel <= median -> 0, else 1), a pyramid made by halving
+ *               both dimensions, and a coarse-to-fine search testing +-1 pixel in
+ *               x and y (9 candidates) per level, the offset doubled per level;
+ *   Sec. III-B  the exclusion bitmap (pixels within +-tol of the median removed),
+ *               the error of a candidate = number of pixels set in
+ *               (MTB_ref XOR MTB_shifted) AND EB_ref AND EB_shifted, and pairwise
+ *               alignment of a stack whose pyramids are built once.
+ *
+ * Readings fixed where the paper is silent (the CUDA code states each again):
+ *   gray      (4899 R + 9617 G + 1868 B + 8192) >> 14, channels in R,G,B order
+ *   shrink    2x2 mean rounded half up; level l is floor(w/2^l) x floor(h/2^l)
+ *   levels    number of pyramid images, full resolution included
+ *   median    lower median (smallest v with cumulative count >= ceil(N/2))
+ *   bitmaps   tb = [g > m], eb = [g < m - tol or g > m + tol]
+ *   shift     exposure i's maps move by (sx, sy): S(b)(x,y) = b(x-sx, y-sy),
+ *             0 outside the image; the reference is never moved
+ *   order     candidate k: 0 = (0,0), then (dx,dy) with dy outer and dx inner
+ *             over -1,0,+1 skipping (0,0); the first minimum in k order wins
+ *   pairs     every exposure i != ref_idx is aligned directly to ref_idx
+ *
+ * Conventions for every entry point:
+ *   - Device pointers are CUDA device (or managed) addresses on the current
+ *     device; host pointers are ordinary (preferably pinned) host memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Device entry points only enqueue work and return; results are valid once
+ *     the stream has reached them.  Host entry points return when done.
+ *   - Images are [n][h][w][3] uint8, RGB interleaved, row pitch 3*w bytes, the
+ *     exposures back to back, base address 16-byte aligned.
+ *   - Shifts are int32 (sx, sy) pairs: the translation to apply to exposure i so
+ *     that it lines up with exposure ref_idx; the ref_idx row is (0, 0).
+ *   - The caller owns every buffer it passes.  The library keeps nothing between
+ *     calls except buffers it allocated and freed on the stream itself.
+ *   - Return value: MTB_OK or one of the negative MTB_ERR_* codes.  Arguments are
+ *     checked before anything is enqueued; an invalid call enqueues nothing.
+ */
+#ifndef MTB_H_
+#define MTB_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MTB_OK 0
+#define MTB_ERR_INVALID_ARG (-1) /* a size, index, tolerance or pointer is out of range */
+#define MTB_ERR_OOM (-2)         /* device or host memory could not be allocated */
+#define MTB_ERR_CUDA (-3)        /* a CUDA call or kernel launch failed */
+#define MTB_ERR_TIMEOUT (-4)     /* a bounded device-side wait gave up */
+#define MTB_ERR_BUSY (-5)        /* a server could not admit work within its budget */
+
+#define MTB_MAX_LEVELS 16
+#define MTB_MAX_EXPOSURES 4096
+#define MTB_MAX_DIM 65535
+
+/* Workspace layout of one stack, in bytes from the workspace base.  Per level l
+ * (0 = full resolution):
+ *   gray plane   uint8 [height[l]][gray_pitch[l]], at gray_offset[l] +
+ *                e * gray_exposure_stride for exposure e
+ *   bit plane    uint32 pairs (tb word, eb word) [height[l]][bits_pitch[l]], at
+ *                bits_offset[l] + e * bits_exposure_stride; bit b of word q of a
+ *                row is pixel 32*q + b; bits at x >= width[l] are 0
+ *   hist         uint32 [n][levels][256]
+ *   median       int32  [n][levels]
+ *   errs         uint32 [n][levels][9]   (candidate errors, reference row 0)
+ *   base         int32  [n][levels][2]   (search offset each level starts from)
+ *   shift        int32  [n][levels][2]   (best shift chosen at each level)
+ *   status       int32 [4]               (device status words) */
+typedef struct mtb_layout {
+    int32_t n, w, h, levels;
+    int32_t tile_levels; /* levels 0..tile_levels-1 come from the pyramid pass */
+    int32_t width[MTB_MAX_LEVELS];
+    int32_t height[MTB_MAX_LEVELS];
+    int32_t gray_pitch[MTB_MAX_LEVELS]; /* bytes per gray row (multiple of 32) */
+    int32_t bits_pitch[MTB_MAX_LEVELS]; /* 8-byte (tb, eb) words per row (even) */
+    uint64_t gray_offset[MTB_MAX_LEVELS];
+    uint64_t gray_exposure_stride;
+    uint64_t bits_offset[MTB_MAX_LEVELS];
+    uint64_t bits_exposure_stride;
+    uint64_t hist_offset;
+    uint64_t median_offset;
+    uint64_t errs_offset;
+    uint64_t base_offset;
+    uint64_t shift_offset;
+    uint64_t status_offset;
+    uint64_t total_bytes;
+} mtb_layout_t;
+
+/* Text for a status code (static storage; never NULL). */
+const char *mtb_status_string(int status);
+
+/* ABI version of this header: 1. */
+int mtb_abi_version(void);
+
+/* Bytes of device workspace one stack needs (0 if the sizes are invalid).
+ * Host only; enqueues nothing. */
+size_t mtb_workspace_bytes(int n_exposures, int w, int h, int levels);
+
+/* Fill *out with the workspace layout of a stack.  Host only. */
+int mtb_workspace_layout(int n_exposures, int w, int h, int levels, mtb_layout_t *out);
+
+/* Align a stack (Sec. III-A, III-B).  images: device [n][h][w][3] uint8;
+ * shifts_out: device int32 [n][2].  The workspace is allocated and freed
+ * stream-ordered (cudaMallocAsync / cudaFreeAsync) on `stream`.
+ * Requires 2 <= n <= MTB_MAX_EXPOSURES, 1 <= w, h <= MTB_MAX_DIM,
+ * 1 <= levels <= MTB_MAX_LEVELS with (w >> (levels-1)) >= 1 and
+ * (h >> (levels-1)) >= 1, 0 <= noise_tol <= 255, 0 <= ref_idx < n. */
+int mtb_align_stack(const uint8_t *images, int n_exposures, int w, int h, int levels,
+                    int noise_tol, int ref_idx, int32_t *shifts_out, void *stream);
+
+/* As mtb_align_stack, plus optional per-level outputs and a caller workspace.
+ * level_errs_out: device uint32 [n][levels][9] or NULL -- the 9 candidate errors
+ *   of every level (Sec. III-A: 9 tests per level), reference row 0.
+ * level_shifts_out: device int32 [n][levels][2] or NULL -- the shift chosen at
+ *   every level; level 0 equals shifts_out.
+ * workspace: device, 256-byte aligned, >= mtb_workspace_bytes(...) bytes, or
+ *   NULL to allocate stream-ordered.  The call overwrites it entirely. */
+int mtb_align_stack_ex(const uint8_t *images, int n_exposures, int w, int h, int levels,
+                       int noise_tol, int ref_idx, int32_t *shifts_out,
+                       uint32_t *level_errs_out, int32_t *level_shifts_out,
+                       void *workspace, size_t workspace_bytes, void *stream);
+
+/* Stage 1 (Sec. III-A gray conversion and pyramid, Sec. III-B histograms):
+ * clears the histogram area, then writes the gray planes and histograms of
+ * levels 0..tile_levels-1 into the workspace. */
+int mtb_build_pyramids(const uint8_t *images, int n_exposures, int w, int h, int levels,
+                       void *workspace, size_t workspace_bytes, void *stream);
+
+/* Stage 2 (Sec. III-A median and MTB, Sec. III-B exclusion bitmap): needs
+ * stage 1 in the same workspace.  Writes medians and both bit planes of every
+ * level, and the gray planes and histograms of levels tile_levels..levels-1. */
+int mtb_build_bitmaps(int n_exposures, int w, int h, int levels, int noise_tol,
+                      void *workspace, size_t workspace_bytes, void *stream);
+
+/* Stage 3 (Sec. III-A coarse-to-fine search, Sec. III-B error count): needs
+ * stage 2 in the same workspace.  Clears the error area, then searches.
+ * Outputs as in mtb_align_stack_ex (each may be NULL). */
+int mtb_search_shifts(int n_exposures, int w, int h, int levels, int ref_idx,
+                      void *workspace, size_t workspace_bytes, int32_t *shifts_out,
+                      uint32_t *level_errs_out, int32_t *level_shifts_out, void *stream);
+
+/* Bytes of device memory mtb_align_stack_host needs: the images, the
+ * workspace and the shifts (0 if the sizes are invalid).  Host only. */
+size_t mtb_host_workspace_bytes(int n_exposures, int w, int h, int levels);
+
+/* Align a stack held in HOST memory (Sec. III-B: the exposures are copied to the
+ * device once).  host_images: host [n][h][w][3] uint8 (pinned memory lets the
+ * copy run asynchronously); host_shifts_out: host int32 [n][2].  The copy in,
+ * the alignment and the copy out are enqueued on `stream`, and the call returns
+ * after synchronising it.  device_workspace: device, 256-byte aligned,
+ * >= mtb_host_workspace_bytes(...) bytes, or NULL to allocate stream-ordered. */
+int mtb_align_stack_host(const uint8_t *host_images, int n_exposures, int w, int h, int levels,
+                         int noise_tol, int ref_idx, int32_t *host_shifts_out,
+                         void *device_workspace, size_t device_workspace_bytes, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MTB_H_ */

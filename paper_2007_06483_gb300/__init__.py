@@ -1,1 +1,250 @@
-"""GB300 median-threshold-bitmap (MTB) exposure alignment."""
+"""GB300 median-threshold-bitmap (MTB) exposure alignment.
+
+Thin ctypes binding over the C ABI of ``include/mtb.h`` (library built in-tree
+by ``paper_2007_06483_gb300.build``).  Every step of the alignment runs in the
+CUDA kernels of that library; this module only marshals arguments.  PyTorch is
+used for device memory and stream handles.  There is no CPU fallback: if the
+library is missing the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional
+
+from .build import LIB_PATH
+
+MTB_OK = 0
+MTB_ERR_INVALID_ARG = -1
+MTB_ERR_OOM = -2
+MTB_ERR_CUDA = -3
+MTB_ERR_TIMEOUT = -4
+MTB_ERR_BUSY = -5
+MTB_MAX_LEVELS = 16
+
+_lock = threading.Lock()
+_lib = None
+
+
+class MtbError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        msg = status_string(status) if _lib is not None else str(status)
+        super().__init__(f"{what}: {msg} ({status})" if what else f"{msg} ({status})")
+
+
+class Layout(ctypes.Structure):
+    """Mirror of mtb_layout_t."""
+
+    _fields_ = [
+        ("n", ctypes.c_int32), ("w", ctypes.c_int32), ("h", ctypes.c_int32), ("levels", ctypes.c_int32),
+        ("tile_levels", ctypes.c_int32),
+        ("width", ctypes.c_int32 * MTB_MAX_LEVELS),
+        ("height", ctypes.c_int32 * MTB_MAX_LEVELS),
+        ("gray_pitch", ctypes.c_int32 * MTB_MAX_LEVELS),
+        ("bits_pitch", ctypes.c_int32 * MTB_MAX_LEVELS),
+        ("gray_offset", ctypes.c_uint64 * MTB_MAX_LEVELS),
+        ("gray_exposure_stride", ctypes.c_uint64),
+        ("bits_offset", ctypes.c_uint64 * MTB_MAX_LEVELS),
+        ("bits_exposure_stride", ctypes.c_uint64),
+        ("hist_offset", ctypes.c_uint64),
+        ("median_offset", ctypes.c_uint64),
+        ("errs_offset", ctypes.c_uint64),
+        ("base_offset", ctypes.c_uint64),
+        ("shift_offset", ctypes.c_uint64),
+        ("status_offset", ctypes.c_uint64),
+        ("total_bytes", ctypes.c_uint64),
+    ]
+
+
+def library_path() -> str:
+    return LIB_PATH
+
+
+def lib():
+    """The loaded C library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library {LIB_PATH} is not built; run paper_2007_06483_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+        sig = {
+            "mtb_status_string": (ctypes.c_char_p, [I]),
+            "mtb_abi_version": (I, []),
+            "mtb_workspace_bytes": (S, [I, I, I, I]),
+            "mtb_workspace_layout": (I, [I, I, I, I, ctypes.POINTER(Layout)]),
+            "mtb_align_stack": (I, [P, I, I, I, I, I, I, P, P]),
+            "mtb_align_stack_ex": (I, [P, I, I, I, I, I, I, P, P, P, P, S, P]),
+            "mtb_build_pyramids": (I, [P, I, I, I, I, P, S, P]),
+            "mtb_build_bitmaps": (I, [I, I, I, I, I, P, S, P]),
+            "mtb_search_shifts": (I, [I, I, I, I, I, P, S, P, P, P, P]),
+            "mtb_host_workspace_bytes": (S, [I, I, I, I]),
+            "mtb_align_stack_host": (I, [P, I, I, I, I, I, I, P, P, S, P]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+        return L
+
+
+def status_string(status: int) -> str:
+    return lib().mtb_status_string(int(status)).decode()
+
+
+def _check(rc: int, what: str):
+    if rc != MTB_OK:
+        raise MtbError(rc, what)
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    return t.data_ptr()
+
+
+def _stream(stream) -> Optional[int]:
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def workspace_bytes(n: int, w: int, h: int, levels: int) -> int:
+    return int(lib().mtb_workspace_bytes(n, w, h, levels))
+
+
+def host_workspace_bytes(n: int, w: int, h: int, levels: int) -> int:
+    return int(lib().mtb_host_workspace_bytes(n, w, h, levels))
+
+
+def layout(n: int, w: int, h: int, levels: int) -> Layout:
+    out = Layout()
+    _check(lib().mtb_workspace_layout(n, w, h, levels, ctypes.byref(out)), "mtb_workspace_layout")
+    return out
+
+
+def _dims(images):
+    import torch
+
+    if not isinstance(images, torch.Tensor) or images.dtype != torch.uint8 or images.dim() != 4 or images.shape[-1] != 3:
+        raise ValueError("images must be a uint8 tensor [n, h, w, 3]")
+    if not images.is_contiguous():
+        raise ValueError("images must be contiguous")
+    n, h, w, _ = images.shape
+    return int(n), int(w), int(h)
+
+
+def new_workspace(n: int, w: int, h: int, levels: int, device="cuda"):
+    import torch
+
+    nbytes = workspace_bytes(n, w, h, levels)
+    if nbytes == 0:
+        raise MtbError(MTB_ERR_INVALID_ARG, "workspace size")
+    return torch.empty(nbytes, dtype=torch.uint8, device=device)
+
+
+def align_stack(images, levels: int, noise_tol: int = 4, ref_idx: int = 0, *, level_outputs: bool = False,
+                workspace=None, stream=None):
+    """Align a [n, h, w, 3] uint8 CUDA stack; returns int32 [n, 2] shifts on the
+    device (and, with level_outputs, uint32 [n, levels, 9] errors and int32
+    [n, levels, 2] per-level shifts)."""
+    import torch
+
+    n, w, h = _dims(images)
+    dev = images.device
+    shifts = torch.empty((n, 2), dtype=torch.int32, device=dev)
+    errs = lsh = None
+    if level_outputs:
+        errs = torch.empty((n, levels, 9), dtype=torch.int32, device=dev)  # viewed as uint32
+        lsh = torch.empty((n, levels, 2), dtype=torch.int32, device=dev)
+    ws_ptr, ws_bytes = None, 0
+    if workspace is not None:
+        ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
+    if errs is None and workspace is None:
+        rc = lib().mtb_align_stack(images.data_ptr(), n, w, h, levels, noise_tol, ref_idx, shifts.data_ptr(),
+                                   _stream(stream))
+    else:
+        rc = lib().mtb_align_stack_ex(images.data_ptr(), n, w, h, levels, noise_tol, ref_idx, shifts.data_ptr(),
+                                      _ptr(errs), _ptr(lsh), ws_ptr, ws_bytes, _stream(stream))
+    _check(rc, "mtb_align_stack")
+    if level_outputs:
+        return shifts, errs, lsh
+    return shifts
+
+
+def build_pyramids(images, levels: int, workspace, stream=None):
+    n, w, h = _dims(images)
+    _check(lib().mtb_build_pyramids(images.data_ptr(), n, w, h, levels, workspace.data_ptr(), workspace.numel(),
+                                    _stream(stream)), "mtb_build_pyramids")
+
+
+def build_bitmaps(n: int, w: int, h: int, levels: int, noise_tol: int, workspace, stream=None):
+    _check(lib().mtb_build_bitmaps(n, w, h, levels, noise_tol, workspace.data_ptr(), workspace.numel(),
+                                   _stream(stream)), "mtb_build_bitmaps")
+
+
+def search_shifts(n: int, w: int, h: int, levels: int, ref_idx: int, workspace, shifts_out=None,
+                  level_errs_out=None, level_shifts_out=None, stream=None):
+    _check(lib().mtb_search_shifts(n, w, h, levels, ref_idx, workspace.data_ptr(), workspace.numel(),
+                                   _ptr(shifts_out), _ptr(level_errs_out), _ptr(level_shifts_out), _stream(stream)),
+           "mtb_search_shifts")
+
+
+def align_stack_host(images, levels: int, noise_tol: int = 4, ref_idx: int = 0, *, device_workspace=None,
+                     stream=None):
+    """Align a host [n, h, w, 3] uint8 stack (torch CPU tensor, ideally pinned);
+    copies in, aligns and copies the shifts back.  Returns int32 [n, 2] (CPU)."""
+    import torch
+
+    n, w, h = _dims(images)
+    out = torch.empty((n, 2), dtype=torch.int32).pin_memory() if images.is_pinned() else \
+        torch.empty((n, 2), dtype=torch.int32)
+    ws_ptr, ws_bytes = None, 0
+    if device_workspace is not None:
+        ws_ptr, ws_bytes = device_workspace.data_ptr(), device_workspace.numel()
+    _check(lib().mtb_align_stack_host(images.data_ptr(), n, w, h, levels, noise_tol, ref_idx, out.data_ptr(),
+                                      ws_ptr, ws_bytes, _stream(stream)), "mtb_align_stack_host")
+    return out
+
+
+def workspace_views(workspace, n: int, w: int, h: int, levels: int) -> dict:
+    """Views of the workspace areas of a stack (torch tensors sharing memory):
+    gray[e][l] uint8 [H_l, gray_pitch_l], bits[e][l] int32 [H_l, bits_pitch_l, 2],
+    hist int32 [n, levels, 256], median int32 [n, levels], errs int32 [n, levels, 9],
+    base / shift int32 [n, levels, 2].  uint32 areas are viewed as int32."""
+    import torch
+
+    lay = layout(n, w, h, levels)
+
+    def area(off, count, dtype, shape):
+        esz = torch.empty((), dtype=dtype).element_size()
+        return workspace[off:off + count * esz].view(dtype).view(*shape)
+
+    gray, bits = [], []
+    for e in range(n):
+        ge, be = [], []
+        for l in range(levels):
+            H, gp, bp = lay.height[l], lay.gray_pitch[l], lay.bits_pitch[l]
+            go = lay.gray_offset[l] + e * lay.gray_exposure_stride
+            bo = lay.bits_offset[l] + e * lay.bits_exposure_stride
+            ge.append(area(go, H * gp, torch.uint8, (H, gp)))
+            be.append(area(bo, H * bp * 2, torch.int32, (H, bp, 2)))
+        gray.append(ge)
+        bits.append(be)
+    return {
+        "layout": lay,
+        "gray": gray,
+        "bits": bits,
+        "hist": area(lay.hist_offset, n * levels * 256, torch.int32, (n, levels, 256)),
+        "median": area(lay.median_offset, n * levels, torch.int32, (n, levels)),
+        "errs": area(lay.errs_offset, n * levels * 9, torch.int32, (n, levels, 9)),
+        "base": area(lay.base_offset, n * levels * 2, torch.int32, (n, levels, 2)),
+        "shift": area(lay.shift_offset, n * levels * 2, torch.int32, (n, levels, 2)),
+    }

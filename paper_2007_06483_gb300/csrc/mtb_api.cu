@@ -1,0 +1,261 @@
+// mtb_api.cu -- the C ABI declared in include/mtb.h: argument checks, the
+// workspace layout and the entry points that enqueue the three stages.
+#include <cstring>
+
+#include "mtb_internal.cuh"
+
+namespace mtb {
+
+namespace {
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+int check_dims(int n, int w, int h, int levels) {
+    if (n < 2 || n > MTB_MAX_EXPOSURES) return MTB_ERR_INVALID_ARG;
+    if (w < 1 || h < 1 || w > MTB_MAX_DIM || h > MTB_MAX_DIM) return MTB_ERR_INVALID_ARG;
+    if (levels < 1 || levels > MTB_MAX_LEVELS) return MTB_ERR_INVALID_ARG;
+    if ((w >> (levels - 1)) < 1 || (h >> (levels - 1)) < 1) return MTB_ERR_INVALID_ARG;
+    return MTB_OK;
+}
+
+int g_sm_count[64] = {0};
+}  // namespace
+
+int device_sm_count() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+    if (g_sm_count[dev] == 0) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 152;
+        g_sm_count[dev] = v;
+    }
+    return g_sm_count[dev];
+}
+
+int check_stack_args(int n, int w, int h, int levels, int noise_tol, int ref_idx) {
+    int rc = check_dims(n, w, h, levels);
+    if (rc != MTB_OK) return rc;
+    if (noise_tol < 0 || noise_tol > 255) return MTB_ERR_INVALID_ARG;
+    if (ref_idx < 0 || ref_idx >= n) return MTB_ERR_INVALID_ARG;
+    return MTB_OK;
+}
+
+int compute_layout(int n, int w, int h, int levels, mtb_layout_t *L) {
+    int rc = check_dims(n, w, h, levels);
+    if (rc != MTB_OK) return rc;
+    std::memset(L, 0, sizeof(*L));
+    L->n = n;
+    L->w = w;
+    L->h = h;
+    L->levels = levels;
+    L->tile_levels = levels < kTileLog2 + 1 ? levels : kTileLog2 + 1;
+    size_t per_exp = 0;
+    for (int l = 0; l < levels; ++l) {
+        L->width[l] = w >> l;
+        L->height[l] = h >> l;
+        L->gray_pitch[l] = (int32_t)align_up((size_t)L->width[l], 32);
+        L->bits_pitch[l] = (int32_t)align_up(((size_t)L->width[l] + 31) / 32, 2);
+        L->gray_offset[l] = per_exp;
+        per_exp += align_up((size_t)L->gray_pitch[l] * L->height[l], 256);
+    }
+    L->gray_exposure_stride = per_exp;
+    size_t off = per_exp * n;
+    size_t bits_per_exp = 0;
+    for (int l = 0; l < levels; ++l) {
+        L->bits_offset[l] = off + bits_per_exp;
+        bits_per_exp += align_up((size_t)L->bits_pitch[l] * 8 * L->height[l], 256);
+    }
+    L->bits_exposure_stride = bits_per_exp;
+    off += bits_per_exp * n;
+    L->hist_offset = off;
+    off += (size_t)n * levels * 256 * sizeof(uint32_t);
+    L->errs_offset = off;
+    off += (size_t)n * levels * 9 * sizeof(uint32_t);
+    off = align_up(off, 256);
+    L->median_offset = off;
+    off = align_up(off + (size_t)n * levels * sizeof(int32_t), 256);
+    L->base_offset = off;
+    off = align_up(off + (size_t)n * levels * 2 * sizeof(int32_t), 256);
+    L->shift_offset = off;
+    off = align_up(off + (size_t)n * levels * 2 * sizeof(int32_t), 256);
+    L->status_offset = off;
+    off = align_up(off + 4 * sizeof(int32_t), 256);
+    L->total_bytes = off;
+    return MTB_OK;
+}
+
+namespace {
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? MTB_OK : MTB_ERR_CUDA; }
+
+int stage_pyramid(const uint8_t *images, const mtb_layout_t &L, uint8_t *ws, cudaStream_t s) {
+    const size_t hist_bytes = (size_t)L.n * L.levels * 256 * sizeof(uint32_t);
+    if (cudaMemsetAsync(ws + L.hist_offset, 0, hist_bytes, s) != cudaSuccess) return MTB_ERR_CUDA;
+    return cuda_status(launch_pyramid(images, L, ws, s));
+}
+
+int stage_search(const mtb_layout_t &L, int ref, uint8_t *ws, int32_t *shifts_out, uint32_t *level_errs_out,
+                 int32_t *level_shifts_out, cudaStream_t s) {
+    const size_t errs_bytes = (size_t)L.n * L.levels * 9 * sizeof(uint32_t);
+    if (cudaMemsetAsync(ws + L.errs_offset, 0, errs_bytes, s) != cudaSuccess) return MTB_ERR_CUDA;
+    return cuda_status(launch_search(L, ref, ws, shifts_out, level_errs_out, level_shifts_out, s));
+}
+
+int run_all(const uint8_t *images, const mtb_layout_t &L, int tol, int ref, uint8_t *ws, int32_t *shifts_out,
+            uint32_t *level_errs_out, int32_t *level_shifts_out, cudaStream_t s) {
+    int rc = stage_pyramid(images, L, ws, s);
+    if (rc != MTB_OK) return rc;
+    rc = cuda_status(launch_bitmaps(L, tol, ws, s));
+    if (rc != MTB_OK) return rc;
+    return stage_search(L, ref, ws, shifts_out, level_errs_out, level_shifts_out, s);
+}
+
+bool misaligned(const void *p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) != 0; }
+
+// Caller workspace if given (checked), else a stream-ordered allocation.
+int acquire(void *given, size_t given_bytes, size_t need, cudaStream_t s, uint8_t **ws, bool *owned) {
+    *owned = false;
+    if (given) {
+        if (given_bytes < need || misaligned(given, 256)) return MTB_ERR_INVALID_ARG;
+        *ws = static_cast<uint8_t *>(given);
+        return MTB_OK;
+    }
+    void *p = nullptr;
+    if (cudaMallocAsync(&p, need, s) != cudaSuccess) {
+        cudaGetLastError();
+        return MTB_ERR_OOM;
+    }
+    *ws = static_cast<uint8_t *>(p);
+    *owned = true;
+    return MTB_OK;
+}
+
+int release(uint8_t *ws, bool owned, cudaStream_t s, int rc) {
+    if (owned && cudaFreeAsync(ws, s) != cudaSuccess && rc == MTB_OK) rc = MTB_ERR_CUDA;
+    return rc;
+}
+
+}  // namespace
+}  // namespace mtb
+
+using namespace mtb;
+
+extern "C" {
+
+const char *mtb_status_string(int status) {
+    switch (status) {
+        case MTB_OK: return "ok";
+        case MTB_ERR_INVALID_ARG: return "invalid argument";
+        case MTB_ERR_OOM: return "out of memory";
+        case MTB_ERR_CUDA: return "CUDA error";
+        case MTB_ERR_TIMEOUT: return "device wait timed out";
+        case MTB_ERR_BUSY: return "over budget";
+        default: return "unknown status";
+    }
+}
+
+int mtb_abi_version(void) { return 1; }
+
+size_t mtb_workspace_bytes(int n_exposures, int w, int h, int levels) {
+    mtb_layout_t L;
+    if (compute_layout(n_exposures, w, h, levels, &L) != MTB_OK) return 0;
+    return L.total_bytes;
+}
+
+int mtb_workspace_layout(int n_exposures, int w, int h, int levels, mtb_layout_t *out) {
+    if (!out) return MTB_ERR_INVALID_ARG;
+    return compute_layout(n_exposures, w, h, levels, out);
+}
+
+int mtb_align_stack_ex(const uint8_t *images, int n_exposures, int w, int h, int levels, int noise_tol,
+                       int ref_idx, int32_t *shifts_out, uint32_t *level_errs_out, int32_t *level_shifts_out,
+                       void *workspace, size_t workspace_bytes, void *stream) {
+    int rc = check_stack_args(n_exposures, w, h, levels, noise_tol, ref_idx);
+    if (rc != MTB_OK) return rc;
+    if (!images || !shifts_out || misaligned(images, 16)) return MTB_ERR_INVALID_ARG;
+    mtb_layout_t L;
+    compute_layout(n_exposures, w, h, levels, &L);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    uint8_t *ws = nullptr;
+    bool owned = false;
+    rc = acquire(workspace, workspace_bytes, L.total_bytes, s, &ws, &owned);
+    if (rc != MTB_OK) return rc;
+    rc = run_all(images, L, noise_tol, ref_idx, ws, shifts_out, level_errs_out, level_shifts_out, s);
+    return release(ws, owned, s, rc);
+}
+
+int mtb_align_stack(const uint8_t *images, int n_exposures, int w, int h, int levels, int noise_tol, int ref_idx,
+                    int32_t *shifts_out, void *stream) {
+    return mtb_align_stack_ex(images, n_exposures, w, h, levels, noise_tol, ref_idx, shifts_out, nullptr, nullptr,
+                              nullptr, 0, stream);
+}
+
+int mtb_build_pyramids(const uint8_t *images, int n_exposures, int w, int h, int levels, void *workspace,
+                       size_t workspace_bytes, void *stream) {
+    mtb_layout_t L;
+    int rc = compute_layout(n_exposures, w, h, levels, &L);
+    if (rc != MTB_OK) return rc;
+    if (!images || misaligned(images, 16) || !workspace || workspace_bytes < L.total_bytes ||
+        misaligned(workspace, 256))
+        return MTB_ERR_INVALID_ARG;
+    return stage_pyramid(images, L, static_cast<uint8_t *>(workspace), static_cast<cudaStream_t>(stream));
+}
+
+int mtb_build_bitmaps(int n_exposures, int w, int h, int levels, int noise_tol, void *workspace,
+                      size_t workspace_bytes, void *stream) {
+    mtb_layout_t L;
+    int rc = compute_layout(n_exposures, w, h, levels, &L);
+    if (rc != MTB_OK) return rc;
+    if (noise_tol < 0 || noise_tol > 255) return MTB_ERR_INVALID_ARG;
+    if (!workspace || workspace_bytes < L.total_bytes || misaligned(workspace, 256)) return MTB_ERR_INVALID_ARG;
+    return cuda_status(launch_bitmaps(L, noise_tol, static_cast<uint8_t *>(workspace),
+                                      static_cast<cudaStream_t>(stream)));
+}
+
+int mtb_search_shifts(int n_exposures, int w, int h, int levels, int ref_idx, void *workspace,
+                      size_t workspace_bytes, int32_t *shifts_out, uint32_t *level_errs_out,
+                      int32_t *level_shifts_out, void *stream) {
+    mtb_layout_t L;
+    int rc = compute_layout(n_exposures, w, h, levels, &L);
+    if (rc != MTB_OK) return rc;
+    if (ref_idx < 0 || ref_idx >= n_exposures) return MTB_ERR_INVALID_ARG;
+    if (!workspace || workspace_bytes < L.total_bytes || misaligned(workspace, 256)) return MTB_ERR_INVALID_ARG;
+    return stage_search(L, ref_idx, static_cast<uint8_t *>(workspace), shifts_out, level_errs_out,
+                        level_shifts_out, static_cast<cudaStream_t>(stream));
+}
+
+size_t mtb_host_workspace_bytes(int n_exposures, int w, int h, int levels) {
+    mtb_layout_t L;
+    if (compute_layout(n_exposures, w, h, levels, &L) != MTB_OK) return 0;
+    const size_t img = align_up((size_t)n_exposures * w * h * 3, 256);
+    return img + L.total_bytes + align_up((size_t)n_exposures * 2 * sizeof(int32_t), 256);
+}
+
+int mtb_align_stack_host(const uint8_t *host_images, int n_exposures, int w, int h, int levels, int noise_tol,
+                         int ref_idx, int32_t *host_shifts_out, void *device_workspace,
+                         size_t device_workspace_bytes, void *stream) {
+    int rc = check_stack_args(n_exposures, w, h, levels, noise_tol, ref_idx);
+    if (rc != MTB_OK) return rc;
+    if (!host_images || !host_shifts_out) return MTB_ERR_INVALID_ARG;
+    mtb_layout_t L;
+    compute_layout(n_exposures, w, h, levels, &L);
+    const size_t img_bytes = (size_t)n_exposures * w * h * 3;
+    const size_t need = mtb_host_workspace_bytes(n_exposures, w, h, levels);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    uint8_t *base = nullptr;
+    bool owned = false;
+    rc = acquire(device_workspace, device_workspace_bytes, need, s, &base, &owned);
+    if (rc != MTB_OK) return rc;
+    uint8_t *d_img = base;
+    uint8_t *ws = base + align_up(img_bytes, 256);
+    int32_t *d_shifts = reinterpret_cast<int32_t *>(ws + L.total_bytes);
+    rc = cuda_status(cudaMemcpyAsync(d_img, host_images, img_bytes, cudaMemcpyHostToDevice, s));
+    if (rc == MTB_OK) rc = run_all(d_img, L, noise_tol, ref_idx, ws, d_shifts, nullptr, nullptr, s);
+    if (rc == MTB_OK)
+        rc = cuda_status(cudaMemcpyAsync(host_shifts_out, d_shifts, (size_t)n_exposures * 2 * sizeof(int32_t),
+                                         cudaMemcpyDeviceToHost, s));
+    rc = release(base, owned, s, rc);
+    if (cudaStreamSynchronize(s) != cudaSuccess && rc == MTB_OK) rc = MTB_ERR_CUDA;
+    return rc;
+}
+
+}  // extern "C"

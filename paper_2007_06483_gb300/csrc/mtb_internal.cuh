@@ -1,0 +1,94 @@
+// mtb_internal.cuh -- definitions shared by the CUDA translation units of the
+// MTB alignment library (never by the CPU oracle).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "mtb.h"
+
+namespace mtb {
+
+// ---------------------------------------------------------------------------
+// Pyramid pass geometry.  One tile is kTileRows x kTileCols full-resolution
+// pixels; because 2^l divides both, every pixel of levels 1..kTileLog2 has its
+// whole 2^l x 2^l source block inside one tile, so a tile builds its part of
+// those levels on chip.  Deeper levels come from the bitmap pass.
+constexpr int kTileLog2 = 5;
+constexpr int kTileRows = 1 << kTileLog2;  // 32
+constexpr int kTileCols = 256;
+constexpr int kPyrThreads = 256;
+constexpr int kPyrWarps = kPyrThreads / 32;
+constexpr int kGroupsPerRow = kTileCols / 16 + 1;  // 16-pixel groups touching one tile row
+
+// Bitmap pass: one CTA turns kBitWordsPerCta output words (32 pixels each) of
+// one (exposure, level) plane into bits.
+constexpr int kBitThreads = 256;
+constexpr int kBitWordsPerCta = 2048;
+
+constexpr int kMaxShiftThreads = 256;
+
+// ---------------------------------------------------------------------------
+// Readings of the paper's unstated points, restated for the device.
+
+// Sec. III-A gray conversion: BT.601 luma weights in Q14, rounded.
+__host__ __device__ __forceinline__ uint32_t luma(uint32_t r, uint32_t g, uint32_t b) {
+    return (4899u * r + 9617u * g + 1868u * b + 8192u) >> 14;
+}
+
+// Sec. III-A halving: mean of a 2x2 block, rounded half up.
+__host__ __device__ __forceinline__ uint32_t box2(uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+    return (a + b + c + d + 2u) >> 2;
+}
+
+// Sec. III-A candidate k of a level: k = 0 is (0,0); k = 1..8 walk the other
+// eight offsets with dy outer and dx inner, each over -1, 0, +1.
+__host__ __device__ __forceinline__ int cand_dx(int k) {
+    int j = k == 0 ? 4 : (k <= 4 ? k - 1 : k);
+    return j % 3 - 1;
+}
+__host__ __device__ __forceinline__ int cand_dy(int k) {
+    int j = k == 0 ? 4 : (k <= 4 ? k - 1 : k);
+    return j / 3 - 1;
+}
+
+// ---------------------------------------------------------------------------
+// Workspace accessors.
+struct Planes {
+    static __device__ __forceinline__ uint8_t *gray(uint8_t *ws, const mtb_layout_t &L, int e, int l) {
+        return ws + L.gray_offset[l] + (size_t)e * L.gray_exposure_stride;
+    }
+    static __device__ __forceinline__ uint2 *bits(uint8_t *ws, const mtb_layout_t &L, int e, int l) {
+        return reinterpret_cast<uint2 *>(ws + L.bits_offset[l] + (size_t)e * L.bits_exposure_stride);
+    }
+    static __device__ __forceinline__ uint32_t *hist(uint8_t *ws, const mtb_layout_t &L, int e, int l) {
+        return reinterpret_cast<uint32_t *>(ws + L.hist_offset) + ((size_t)e * L.levels + l) * 256;
+    }
+    static __device__ __forceinline__ int32_t *median(uint8_t *ws, const mtb_layout_t &L, int e, int l) {
+        return reinterpret_cast<int32_t *>(ws + L.median_offset) + (size_t)e * L.levels + l;
+    }
+    static __device__ __forceinline__ uint32_t *errs(uint8_t *ws, const mtb_layout_t &L, int e, int l) {
+        return reinterpret_cast<uint32_t *>(ws + L.errs_offset) + ((size_t)e * L.levels + l) * 9;
+    }
+    static __device__ __forceinline__ int32_t *base(uint8_t *ws, const mtb_layout_t &L, int e, int l) {
+        return reinterpret_cast<int32_t *>(ws + L.base_offset) + ((size_t)e * L.levels + l) * 2;
+    }
+    static __device__ __forceinline__ int32_t *shift(uint8_t *ws, const mtb_layout_t &L, int e, int l) {
+        return reinterpret_cast<int32_t *>(ws + L.shift_offset) + ((size_t)e * L.levels + l) * 2;
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Host-side launchers (each returns a cudaError_t of the launch).
+int compute_layout(int n, int w, int h, int levels, mtb_layout_t *L);
+int check_stack_args(int n, int w, int h, int levels, int noise_tol, int ref_idx);
+
+cudaError_t launch_pyramid(const uint8_t *images, const mtb_layout_t &L, uint8_t *ws, cudaStream_t s);
+cudaError_t launch_bitmaps(const mtb_layout_t &L, int noise_tol, uint8_t *ws, cudaStream_t s);
+cudaError_t launch_search(const mtb_layout_t &L, int ref_idx, uint8_t *ws, int32_t *shifts_out,
+                          uint32_t *level_errs_out, int32_t *level_shifts_out, cudaStream_t s);
+
+int device_sm_count();
+
+}  // namespace mtb

@@ -1,0 +1,117 @@
+"""The C-ABI library without a GPU: it loads, exports every function the header
+declares, checks arguments before touching the device, and lays the workspace
+out as documented."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", f) for f in sorted(os.listdir(os.path.join(ROOT, "include")))
+           if f.endswith(".h")]
+
+
+def declared_functions():
+    names = []
+    for h in HEADERS:
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"\b(mtb_\w+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_header_declares_the_core_call():
+    names = declared_functions()
+    assert "mtb_align_stack" in names
+    assert len(names) >= 10
+
+
+def test_every_declared_symbol_is_exported(mtb_lib):
+    lib = ctypes.CDLL(mtb_lib.library_path())
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_status_strings(mtb_lib):
+    for code in (0, -1, -2, -3, -4, -5):
+        assert mtb_lib.status_string(code) not in ("", "unknown status")
+    assert mtb_lib.status_string(12345) == "unknown status"
+    assert mtb_lib.lib().mtb_abi_version() == 1
+
+
+@pytest.mark.parametrize("n,w,h,levels,tol,ref", [
+    (1, 64, 64, 3, 4, 0),      # one exposure: nothing to align
+    (2, 0, 64, 3, 4, 0),
+    (2, 64, 0, 3, 4, 0),
+    (2, 65536, 4, 1, 4, 0),    # wider than MTB_MAX_DIM
+    (2, 64, 64, 0, 4, 0),
+    (2, 64, 64, 17, 4, 0),     # more than MTB_MAX_LEVELS
+    (2, 64, 64, 8, 4, 0),      # 64 >> 7 == 0: coarsest level empty
+    (2, 64, 64, 3, -1, 0),
+    (2, 64, 64, 3, 256, 0),
+    (2, 64, 64, 3, 4, 2),
+    (2, 64, 64, 3, 4, -1),
+])
+def test_invalid_arguments_rejected_on_host(mtb_lib, n, w, h, levels, tol, ref):
+    lib = mtb_lib.lib()
+    # pointers are never dereferenced: the checks run before any CUDA call
+    fake = 1 << 20
+    rc = lib.mtb_align_stack(fake, n, w, h, levels, tol, ref, fake, None)
+    assert rc == mtb_lib.MTB_ERR_INVALID_ARG
+    rc = lib.mtb_align_stack_host(fake, n, w, h, levels, tol, ref, fake, None, 0, None)
+    assert rc == mtb_lib.MTB_ERR_INVALID_ARG
+
+
+def test_null_and_misaligned_pointers_rejected_on_host(mtb_lib):
+    lib = mtb_lib.lib()
+    assert lib.mtb_align_stack(None, 2, 64, 64, 3, 4, 0, 1 << 20, None) == mtb_lib.MTB_ERR_INVALID_ARG
+    assert lib.mtb_align_stack(1 << 20, 2, 64, 64, 3, 4, 0, None, None) == mtb_lib.MTB_ERR_INVALID_ARG
+    assert lib.mtb_align_stack((1 << 20) + 8, 2, 64, 64, 3, 4, 0, 1 << 20, None) == mtb_lib.MTB_ERR_INVALID_ARG
+    nbytes = mtb_lib.workspace_bytes(2, 64, 64, 3)
+    # workspace too small / misaligned
+    assert lib.mtb_align_stack_ex(1 << 20, 2, 64, 64, 3, 4, 0, 1 << 20, None, None, 1 << 24, nbytes - 1,
+                                  None) == mtb_lib.MTB_ERR_INVALID_ARG
+    assert lib.mtb_align_stack_ex(1 << 20, 2, 64, 64, 3, 4, 0, 1 << 20, None, None, (1 << 24) + 64, nbytes,
+                                  None) == mtb_lib.MTB_ERR_INVALID_ARG
+    assert lib.mtb_build_pyramids(1 << 20, 2, 64, 64, 3, None, nbytes, None) == mtb_lib.MTB_ERR_INVALID_ARG
+    assert lib.mtb_build_bitmaps(2, 64, 64, 3, 300, 1 << 24, nbytes, None) == mtb_lib.MTB_ERR_INVALID_ARG
+    assert lib.mtb_search_shifts(2, 64, 64, 3, 5, 1 << 24, nbytes, None, None, None,
+                                 None) == mtb_lib.MTB_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("n,w,h,levels", [(2, 1, 1, 1), (3, 37, 23, 3), (7, 6000, 4000, 8), (2, 65535, 2, 2),
+                                          (5, 777, 555, 9), (2, 1024, 1024, 11)])
+def test_layout_invariants(mtb_lib, n, w, h, levels):
+    lay = mtb_lib.layout(n, w, h, levels)
+    assert mtb_lib.workspace_bytes(n, w, h, levels) == lay.total_bytes
+    assert lay.tile_levels == min(levels, 6)
+    regions = []
+    for l in range(levels):
+        assert lay.width[l] == w >> l and lay.height[l] == h >> l
+        assert lay.gray_pitch[l] % 32 == 0 and lay.gray_pitch[l] >= lay.width[l]
+        assert lay.bits_pitch[l] % 2 == 0 and lay.bits_pitch[l] * 32 >= lay.width[l]
+        for e in range(n):
+            go = lay.gray_offset[l] + e * lay.gray_exposure_stride
+            bo = lay.bits_offset[l] + e * lay.bits_exposure_stride
+            assert go % 256 == 0 and bo % 256 == 0
+            regions.append((go, go + lay.gray_pitch[l] * lay.height[l]))
+            regions.append((bo, bo + lay.bits_pitch[l] * 8 * lay.height[l]))
+    regions.append((lay.hist_offset, lay.hist_offset + n * levels * 256 * 4))
+    regions.append((lay.errs_offset, lay.errs_offset + n * levels * 9 * 4))
+    regions.append((lay.median_offset, lay.median_offset + n * levels * 4))
+    regions.append((lay.base_offset, lay.base_offset + n * levels * 8))
+    regions.append((lay.shift_offset, lay.shift_offset + n * levels * 8))
+    regions.append((lay.status_offset, lay.status_offset + 16))
+    regions.sort()
+    for (a0, a1), (b0, b1) in zip(regions, regions[1:]):
+        assert a1 <= b0, "workspace regions overlap"
+    assert regions[-1][1] <= lay.total_bytes
+    host = mtb_lib.host_workspace_bytes(n, w, h, levels)
+    assert host >= lay.total_bytes + n * w * h * 3 + n * 8
+
+
+def test_invalid_sizes_give_zero_workspace(mtb_lib):
+    assert mtb_lib.workspace_bytes(1, 64, 64, 3) == 0
+    assert mtb_lib.workspace_bytes(2, 64, 64, 8) == 0
+    assert mtb_lib.host_workspace_bytes(2, 0, 64, 1) == 0
