@@ -1,0 +1,425 @@
+#!/usr/bin/env python3
+"""Benchmark of the MTB alignment hot path on one or more GB300s.
+
+A step is one pass of the whole path over one exposure stack: the pyramid pass,
+the bitmap pass and the coarse-to-fine shift search, each a C-ABI call
+(mtb_build_pyramids, mtb_build_bitmaps, mtb_search_shifts) on the same stream
+with CUDA events between them.  The default workload is the 4000x3000 stack of
+3 exposures (2 pairs, 7 levels).  The metric is aligned MPix/s: full-resolution
+pixels of every aligned pair divided by the step time.
+
+Inputs and workspaces rotate over several device copies, so between two uses of
+one buffer more than 3x the L2 capacity is written and read: every step starts
+with its data in HBM.  `e2e` times the host-buffer entry point
+(mtb_align_stack_host) from pinned host memory: copy in, align, copy the shifts
+out.  `cpu_baseline` times the single-threaded oracle on the same stack.
+
+Multi-GPU (torchrun): each rank aligns its own stack every step (weak scaling,
+no collective on the data path); the barrier and the max over ranks of the
+timed region are the only cross-rank operations.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import dataclasses
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "aligned MPix/s per exposure pair"
+UNIT = "MPix/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
+# ncu capture, keyed by kernel and workload, with the SHA-256 of the kernel's
+# source file at capture time; reported only while the source is unchanged.
+NCU_TRAFFIC = {
+    ("pyramid", "stack4000x3000x3"): {"bytes": 118_509_312,
+                                      "source_sha256": "6ab5c5c941879a5e196e704dcc18dd564efc6a4f310e8f94047ae8ce0104aace"},
+}
+
+
+def parse_args(argv=None):
+    p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=50)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=("gb300", "reference"), default="gb300")
+    p.add_argument("--workload", default="stack4000x3000x3")
+    p.add_argument("--buffers", type=int, default=4, help="device copies rotated over the steps")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args(argv)
+
+
+# ----------------------------------------------------------------------------- distributed
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def shard_units(total_units: int, rank: int, world: int):
+    """Units (stacks) of one step given to `rank`: contiguous, balanced."""
+    lo = total_units * rank // world
+    hi = total_units * (rank + 1) // world
+    return list(range(lo, hi))
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+# ----------------------------------------------------------------------------- workload
+def workload(name: str):
+    from paper_2007_06483_gb300 import synth
+
+    for spec in synth.PLAIN_CONFIGS:
+        if spec.name == name:
+            return spec
+    raise SystemExit(f"unknown workload {name}; choose from {[s.name for s in synth.PLAIN_CONFIGS]}")
+
+
+def algorithmic_bytes(spec) -> dict:
+    """Bytes each stage must move for one stack (per step), by the path's design:
+    pyramid: read RGB (3 B/px) + write gray of levels 0..min(L-1, 5);
+    bitmaps: read every gray level (1 B/px) + write tb and eb (2 bits/px), plus
+             the deep levels' own gray writes;
+    search:  read tb and eb of both exposures at every level (4 bits/px/pair)."""
+    n, L = spec.n, spec.levels
+    px = [(spec.w >> l) * (spec.h >> l) for l in range(L)]
+    tile = min(L, 6)
+    pyr = n * (3 * px[0] + sum(px[:tile]))
+    bit = n * (sum(px) + sum(px) / 4 + sum(px[tile:]))
+    srch = spec.pairs * sum(px) / 2
+    return {"pyramid": pyr, "bitmaps": bit, "search": srch}
+
+
+def kernels_per_step(spec) -> int:
+    return 1 + 1 + spec.levels + 1  # pyramid, bitmaps, one shift launch per level, finalize
+
+
+def stage_kernel_source(stage: str) -> str:
+    return os.path.join(ROOT, "paper_2007_06483_gb300", "csrc",
+                        {"pyramid": "mtb_pyramid.cu", "bitmaps": "mtb_bitmaps.cu", "search": "mtb_search.cu"}[stage])
+
+
+def traffic_for(stage: str, spec):
+    rec = NCU_TRAFFIC.get((stage, spec.name))
+    if not rec:
+        return None
+    digest = hashlib.sha256(open(stage_kernel_source(stage), "rb").read()).hexdigest()
+    return rec["bytes"] if rec["source_sha256"] == digest else None
+
+
+def hbm_peak():
+    try:
+        peaks = json.load(open(PEAKS_FILE))
+        return float(peaks["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="mtb_clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu=timestamp,{self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "50", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self) -> dict:
+        if self.proc is not None:
+            time.sleep(0.1)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+            os.unlink(self.path)
+        except Exception:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[j] for r in rows for j in range(4) if r[5 + j].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------- CPU baseline
+def oracle_rate(images_np, spec, budget_s: float = 12.0, max_s: float = 30.0) -> dict:
+    """Single-threaded oracle on the same stack, repeated to about budget_s."""
+    import oracle
+
+    t0 = time.perf_counter()
+    res = oracle.align_stack(images_np, spec.levels, spec.noise_tol, spec.ref)
+    first = time.perf_counter() - t0
+    reps = 1
+    total = first
+    while total + first <= min(budget_s, max_s):
+        oracle.align_stack(images_np, spec.levels, spec.noise_tol, spec.ref)
+        reps += 1
+        total = time.perf_counter() - t0
+    rate = spec.aligned_pixels * reps / total / 1e6
+    return {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{reps} x full {spec.name} stack ({spec.pairs} pairs), single-threaded C oracle, {total:.1f} s",
+            "result": res}
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def run_gb300(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local if world > 1 else torch.cuda.current_device())
+    torch.cuda.set_device(dev)
+
+    from paper_2007_06483_gb300 import build as cuda_build
+
+    cuda_build.build()
+    import paper_2007_06483_gb300 as mtb
+    from paper_2007_06483_gb300 import synth
+
+    base = workload(args.workload)
+    units = shard_units(world, rank, world)  # one stack per rank per step
+    spec = dataclasses.replace(base, seed=base.seed + 1000 * units[0]) if units[0] else base
+    n, w, h, L = spec.n, spec.w, spec.h, spec.levels
+    images = synth.make_stack(spec, dev)
+    B = max(1, args.buffers)
+    imgs = [images] + [images.clone() for _ in range(B - 1)]
+    wss = [mtb.new_workspace(n, w, h, L, device=dev) for _ in range(B)]
+    shifts = [torch.empty((n, 2), dtype=torch.int32, device=dev) for _ in range(B)]
+    stream = torch.cuda.current_stream(dev)
+
+    def step(b, ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        mtb.build_pyramids(imgs[b], L, wss[b], stream)
+        if ev is not None:
+            ev[1].record(stream)
+        mtb.build_bitmaps(n, w, h, L, spec.noise_tol, wss[b], stream)
+        if ev is not None:
+            ev[2].record(stream)
+        mtb.search_shifts(n, w, h, L, spec.ref, wss[b], shifts[b], None, None, stream)
+        if ev is not None:
+            ev[3].record(stream)
+
+    for k in range(max(3, args.warmup)):
+        step(k % B)
+    torch.cuda.synchronize(dev)
+
+    K = args.steps
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+    sampler = ClockSampler(dev.index if dev.index is not None else 0)
+    sampler.start()
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    t_wall = time.perf_counter()
+    for k in range(K):
+        step(k % B, evs[k])
+    torch.cuda.synchronize(dev)
+    t_wall = time.perf_counter() - t_wall
+    barrier(world)
+    clocks = sampler.stop()
+
+    total_ms = evs[0][0].elapsed_time(evs[-1][3])
+    step_ms = [e[0].elapsed_time(e[3]) for e in evs]
+    stage_ms = {
+        "pyramid": statistics.mean(e[0].elapsed_time(e[1]) for e in evs),
+        "bitmaps": statistics.mean(e[1].elapsed_time(e[2]) for e in evs),
+        "search": statistics.mean(e[2].elapsed_time(e[3]) for e in evs),
+    }
+    total_ms = max_over_ranks(total_ms, world, dev)
+    ms_per_step = total_ms / K
+    value = world * spec.aligned_pixels / (ms_per_step / 1e3) / 1e6
+
+    # correctness of what was timed: every buffer's shifts vs the planted ones
+    want = synth.expected_shifts(spec)
+    planted_ok = all(np.array_equal(s.cpu().numpy(), want) for s in shifts)
+
+    abytes = algorithmic_bytes(spec)
+    peak, peak_kind = hbm_peak()
+    dom = max(stage_ms, key=stage_ms.get)
+    achieved = abytes[dom] / (stage_ms[dom] / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": {"pyramid": "k_pyramid", "bitmaps": "k_bitmaps",
+                                           "search": "k_shift x levels + k_finalize"}[dom],
+                "achieved": round(achieved, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic_for(dom, spec),
+                "algorithmic_bytes_per_launch": abytes[dom]}
+    stages = {k: {"ms": round(v, 5), "alg_GBps": round(abytes[k] / (v / 1e3) / 1e9, 1),
+                  "frac_of_peak": round(abytes[k] / (v / 1e3) / 1e9 / peak, 4)} for k, v in stage_ms.items()}
+    step_bytes = sum(abytes.values())
+
+    # ---- end to end through the host-buffer entry point ----
+    e2e = None
+    if not args.no_e2e:
+        host = images.cpu().pin_memory()
+        dws = torch.empty(mtb.host_workspace_bytes(n, w, h, L), dtype=torch.uint8, device=dev)
+        for _ in range(2):
+            mtb.align_stack_host(host, L, spec.noise_tol, spec.ref, device_workspace=dws, stream=stream)
+        Ke = max(3, min(K, 20))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier(world)
+        e0.record(stream)
+        for _ in range(Ke):
+            out = mtb.align_stack_host(host, L, spec.noise_tol, spec.ref, device_workspace=dws, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        e_ms = max_over_ranks(e0.elapsed_time(e1) / Ke, world, dev)
+        planted_ok = planted_ok and np.array_equal(out.numpy(), want)
+        e2e = {"value": round(world * spec.aligned_pixels / (e_ms / 1e3) / 1e6, 2), "unit": UNIT,
+               "ms_per_step": round(e_ms, 4), "h2d_bytes_per_step": int(host.numel()),
+               "d2h_bytes_per_step": int(out.numel() * out.element_size()), "steps": Ke}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        res = oracle_rate(images.cpu().numpy(), spec)
+        gpu_match = all(np.array_equal(s.cpu().numpy(), res["result"]["shifts"]) for s in shifts)
+        cpu = {k: v for k, v in res.items() if k != "result"}
+        cpu["value"] = round(cpu["value"], 3)
+        cpu["gpu_shifts_equal_oracle"] = bool(gpu_match)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": spec.name, "w": w, "h": h, "n_exposures": n, "pairs": spec.pairs,
+                       "levels": L, "noise_tol": spec.noise_tol, "ref": spec.ref,
+                       "stacks_per_step_per_gpu": 1, "parallelism": f"replicas x{world}",
+                       "l2": f"inputs+workspaces rotate over {B} device copies "
+                             f"({B * (spec.input_bytes + wss[0].numel()) / 1e6:.0f} MB > L2)"},
+            "latency_ms": {"p50": round(statistics.median(step_ms), 5),
+                           "p99": round(sorted(step_ms)[min(len(step_ms) - 1, int(math.ceil(0.99 * len(step_ms))) - 1)], 5)},
+            "hbm_gbs": round(step_bytes / (ms_per_step / 1e3) / 1e9, 1),
+            "stages": stages,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": K * kernels_per_step(spec),
+            "clocks": clocks,
+            "planted_shifts_recovered": bool(planted_ok),
+            "wall_s_timed_region": round(t_wall, 4),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    """The oracle as it stands, on the host cores, on the same workload and metric.
+    A step aligns one exposure pair of the stack (the reference and the next
+    exposure, both pyramids built) -- the unit of the metric."""
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    from paper_2007_06483_gb300 import synth
+
+    spec = workload(args.workload)
+    images = synth.make_stack(spec).numpy()
+    other = (spec.ref + 1) % spec.n
+    pair = np.ascontiguousarray(images[[spec.ref, other]])
+    t = time.perf_counter()
+    oracle.align_stack(pair, spec.levels, spec.noise_tol, 0)
+    one = time.perf_counter() - t
+    # keep the whole run within about three minutes: crop rows if a step is too slow
+    budget = 150.0
+    rows = spec.h
+    if one * (args.steps + args.warmup) > budget:
+        rows = max(1 << (spec.levels - 1), int(spec.h * budget / (one * (args.steps + args.warmup))))
+        pair = np.ascontiguousarray(pair[:, :rows])
+    for _ in range(args.warmup):
+        oracle.align_stack(pair, spec.levels, spec.noise_tol, 0)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.align_stack(pair, spec.levels, spec.noise_tol, 0)
+    dt = (time.perf_counter() - t) / args.steps
+    px = spec.w * rows
+    value = px / dt / 1e6
+    sample = f"one {spec.w}x{rows} exposure pair of {spec.name} per step, single-threaded C oracle"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": spec.name, "w": spec.w, "h": spec.h, "n_exposures": spec.n, "pairs": spec.pairs,
+                   "levels": spec.levels, "noise_tol": spec.noise_tol, "ref": spec.ref},
+        "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gb300(args)
+
+
+if __name__ == "__main__":
+    main()
