@@ -162,6 +162,28 @@ int mtb_align_stack_host(const uint8_t *host_images, int n_exposures, int w, int
                          int noise_tol, int ref_idx, int32_t *host_shifts_out,
                          void *device_workspace, size_t device_workspace_bytes, void *stream);
 
+/* Size of the fixed device scratch array used by mtb_align_stack_noalloc:
+ * 32 MiB, enough for a stack of five 3.7 MP exposures at 6 levels. */
+#define MTB_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+
+/* mtb_align_stack_ex for callers that cannot allocate device memory when they
+ * align (a per-frame loop with a deadline, a plug-in whose host owns all
+ * allocations, a fixed memory budget).  The paper has no counterpart; this is a
+ * property of the library.  Arguments and outputs as in mtb_align_stack_ex
+ * (level_errs_out and level_shifts_out may be NULL); no cudaMalloc, cudaFree or
+ * other allocating call is made.  The workspace is a fixed device array of
+ * MTB_NOALLOC_SCRATCH_BYTES that each device holds from the first call on it
+ * until the process exits.
+ * - A stack whose mtb_workspace_bytes() exceeds MTB_NOALLOC_SCRATCH_BYTES is
+ *   rejected with MTB_ERR_INVALID_ARG before anything is enqueued.
+ * - The first call on a device looks the array's address up (cudaGetSymbolAddress)
+ *   with that device current; make that first call before any stream capture.
+ * - All calls on a device share the array.  Calls whose GPU work overlaps (other
+ *   streams, other host threads) race and give wrong results: order them. */
+int mtb_align_stack_noalloc(const uint8_t *images, int n_exposures, int w, int h, int levels,
+                            int noise_tol, int ref_idx, int32_t *shifts_out,
+                            uint32_t *level_errs_out, int32_t *level_shifts_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -248,3 +248,32 @@ def workspace_views(workspace, n: int, w: int, h: int, levels: int) -> dict:
         "base": area(lay.base_offset, n * levels * 2, torch.int32, (n, levels, 2)),
         "shift": area(lay.shift_offset, n * levels * 2, torch.int32, (n, levels, 2)),
     }
+
+
+_noalloc_fn = None
+
+
+def align_stack_noalloc(images, levels: int, noise_tol: int = 4, ref_idx: int = 0, *, stream=None):
+    """mtb_align_stack_noalloc: the same alignment with the library's fixed device
+    scratch array as workspace, for callers that cannot allocate device memory
+    while aligning.  The output tensors are the caller's (allocated here by
+    torch).  Returns (shifts [n,2], level errors [n,levels,9] viewed as int32,
+    level shifts [n,levels,2]).  Stacks larger than MTB_NOALLOC_SCRATCH_BYTES of
+    workspace are rejected; calls that overlap on the GPU race on the array."""
+    global _noalloc_fn
+    import torch
+
+    if _noalloc_fn is None:
+        fn = lib().mtb_align_stack_noalloc
+        P, I = ctypes.c_void_p, ctypes.c_int
+        fn.restype = I
+        fn.argtypes = [P, I, I, I, I, I, I, P, P, P, P]
+        _noalloc_fn = fn
+    n, w, h = _dims(images)
+    dev = images.device
+    shifts = torch.empty((n, 2), dtype=torch.int32, device=dev)
+    errs = torch.empty((n, levels, 9), dtype=torch.int32, device=dev)
+    lsh = torch.empty((n, levels, 2), dtype=torch.int32, device=dev)
+    _check(_noalloc_fn(images.data_ptr(), n, w, h, levels, noise_tol, ref_idx, shifts.data_ptr(), errs.data_ptr(),
+                       lsh.data_ptr(), _stream(stream)), "mtb_align_stack_noalloc")
+    return shifts, errs, lsh
