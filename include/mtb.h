@@ -74,6 +74,9 @@ extern "C" {
  *   errs         uint32 [n][levels][9]   (candidate errors, reference row 0)
  *   base         int32  [n][levels][2]   (search offset each level starts from)
  *   shift        int32  [n][levels][2]   (best shift chosen at each level)
+ *   table        uint32 [n][1280]         (candidate errors of whole search windows
+ *                                         at the coarsest levels, per pair)
+ *   counters     int32  [n * (levels + 2) + 16] (completion counters of the kernels)
  *   status       int32 [4]               (device status words) */
 typedef struct mtb_layout {
     int32_t n, w, h, levels;
@@ -91,6 +94,8 @@ typedef struct mtb_layout {
     uint64_t errs_offset;
     uint64_t base_offset;
     uint64_t shift_offset;
+    uint64_t table_offset;
+    uint64_t counter_offset;
     uint64_t status_offset;
     uint64_t total_bytes;
 } mtb_layout_t;
@@ -130,23 +135,39 @@ int mtb_align_stack_ex(const uint8_t *images, int n_exposures, int w, int h, int
                        void *workspace, size_t workspace_bytes, void *stream);
 
 /* Stage 1 (Sec. III-A gray conversion and pyramid, Sec. III-B histograms):
- * clears the histogram area, then writes the gray planes and histograms of
- * levels 0..tile_levels-1 into the workspace. */
+ * clears the histogram and counter areas, then writes the gray planes,
+ * histograms and medians of levels 0..tile_levels-1 into the workspace. */
 int mtb_build_pyramids(const uint8_t *images, int n_exposures, int w, int h, int levels,
                        void *workspace, size_t workspace_bytes, void *stream);
 
 /* Stage 2 (Sec. III-A median and MTB, Sec. III-B exclusion bitmap): needs
- * stage 1 in the same workspace.  Writes medians and both bit planes of every
- * level, and the gray planes and histograms of levels tile_levels..levels-1. */
+ * stage 1 in the same workspace.  Writes both bit planes of every level, and
+ * the gray planes, histograms and medians of levels tile_levels..levels-1. */
 int mtb_build_bitmaps(int n_exposures, int w, int h, int levels, int noise_tol,
                       void *workspace, size_t workspace_bytes, void *stream);
 
 /* Stage 3 (Sec. III-A coarse-to-fine search, Sec. III-B error count): needs
- * stage 2 in the same workspace.  Clears the error area, then searches.
- * Outputs as in mtb_align_stack_ex (each may be NULL). */
+ * stage 2 in the same workspace.  Outputs as in mtb_align_stack_ex (each may be
+ * NULL); overwrites the error, base and shift areas. */
 int mtb_search_shifts(int n_exposures, int w, int h, int levels, int ref_idx,
                       void *workspace, size_t workspace_bytes, int32_t *shifts_out,
                       uint32_t *level_errs_out, int32_t *level_shifts_out, void *stream);
+
+/* Status word of the last search run in `workspace` (sizes as when it ran):
+ * MTB_OK, or MTB_ERR_TIMEOUT if a bounded device-side wait gave up.  Waits for
+ * `stream` first, then copies 4 bytes to the host.  Device-side waits only end
+ * by timeout if the library has a bug; the results of such a run are invalid. */
+int mtb_workspace_status(const void *workspace, size_t workspace_bytes, int n_exposures, int w, int h, int levels,
+                         void *stream);
+
+/* Test hook with no counterpart in the paper: runs the search of stage 3 with
+ * pair 0's coarse-level work withholding its completion signal, so the work that
+ * depends on it waits until timeout_ns (1 ns .. 1 s) runs out.  Returns the
+ * status afterwards: MTB_ERR_TIMEOUT shows that the bounded waits end and
+ * report instead of hanging.  Needs stage 2 in the workspace and at least one
+ * coarse level (MTB_ERR_INVALID_ARG otherwise); outputs nothing. */
+int mtb_debug_search_withheld(int n_exposures, int w, int h, int levels, int ref_idx, void *workspace,
+                              size_t workspace_bytes, long long timeout_ns, void *stream);
 
 /* Bytes of device memory mtb_align_stack_host needs: the images, the
  * workspace and the shifts (0 if the sizes are invalid).  Host only. */

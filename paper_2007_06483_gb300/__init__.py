@@ -53,6 +53,8 @@ class Layout(ctypes.Structure):
         ("errs_offset", ctypes.c_uint64),
         ("base_offset", ctypes.c_uint64),
         ("shift_offset", ctypes.c_uint64),
+        ("table_offset", ctypes.c_uint64),
+        ("counter_offset", ctypes.c_uint64),
         ("status_offset", ctypes.c_uint64),
         ("total_bytes", ctypes.c_uint64),
     ]
@@ -84,6 +86,8 @@ def lib():
             "mtb_search_shifts": (I, [I, I, I, I, I, P, S, P, P, P, P]),
             "mtb_host_workspace_bytes": (S, [I, I, I, I]),
             "mtb_align_stack_host": (I, [P, I, I, I, I, I, I, P, P, S, P]),
+            "mtb_workspace_status": (I, [P, S, I, I, I, I, P]),
+            "mtb_debug_search_withheld": (I, [I, I, I, I, I, P, S, ctypes.c_longlong, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -195,6 +199,12 @@ def search_shifts(n: int, w: int, h: int, levels: int, ref_idx: int, workspace, 
     _check(lib().mtb_search_shifts(n, w, h, levels, ref_idx, workspace.data_ptr(), workspace.numel(),
                                    _ptr(shifts_out), _ptr(level_errs_out), _ptr(level_shifts_out), _stream(stream)),
            "mtb_search_shifts")
+
+
+def workspace_status(workspace, n: int, w: int, h: int, levels: int, stream=None) -> int:
+    """Status word of the last search in `workspace` (MTB_OK or MTB_ERR_TIMEOUT)."""
+    return int(lib().mtb_workspace_status(workspace.data_ptr(), workspace.numel(), n, w, h, levels,
+                                          _stream(stream)))
 
 
 def align_stack_host(images, levels: int, noise_tol: int = 4, ref_idx: int = 0, *, device_workspace=None,

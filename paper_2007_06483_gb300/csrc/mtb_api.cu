@@ -68,6 +68,9 @@ int compute_layout(int n, int w, int h, int levels, mtb_layout_t *L) {
     off += bits_per_exp * n;
     L->hist_offset = off;
     off += (size_t)n * levels * 256 * sizeof(uint32_t);
+    L->counter_offset = off;  // right after hist: the pyramid stage clears both in one launch
+    off += (size_t)(n * (levels + 2) + 16) * sizeof(int32_t);
+    off = align_up(off, 256);
     L->errs_offset = off;
     off += (size_t)n * levels * 9 * sizeof(uint32_t);
     off = align_up(off, 256);
@@ -77,6 +80,8 @@ int compute_layout(int n, int w, int h, int levels, mtb_layout_t *L) {
     off = align_up(off + (size_t)n * levels * 2 * sizeof(int32_t), 256);
     L->shift_offset = off;
     off = align_up(off + (size_t)n * levels * 2 * sizeof(int32_t), 256);
+    L->table_offset = off;
+    off = align_up(off + (size_t)n * kTableWords * sizeof(uint32_t), 256);
     L->status_offset = off;
     off = align_up(off + 4 * sizeof(int32_t), 256);
     L->total_bytes = off;
@@ -88,25 +93,16 @@ namespace {
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? MTB_OK : MTB_ERR_CUDA; }
 
 int stage_pyramid(const uint8_t *images, const mtb_layout_t &L, uint8_t *ws, cudaStream_t s) {
-    const size_t hist_bytes = (size_t)L.n * L.levels * 256 * sizeof(uint32_t);
-    if (cudaMemsetAsync(ws + L.hist_offset, 0, hist_bytes, s) != cudaSuccess) return MTB_ERR_CUDA;
     return cuda_status(launch_pyramid(images, L, ws, s));
-}
-
-int stage_search(const mtb_layout_t &L, int ref, uint8_t *ws, int32_t *shifts_out, uint32_t *level_errs_out,
-                 int32_t *level_shifts_out, cudaStream_t s) {
-    const size_t errs_bytes = (size_t)L.n * L.levels * 9 * sizeof(uint32_t);
-    if (cudaMemsetAsync(ws + L.errs_offset, 0, errs_bytes, s) != cudaSuccess) return MTB_ERR_CUDA;
-    return cuda_status(launch_search(L, ref, ws, shifts_out, level_errs_out, level_shifts_out, s));
 }
 
 int run_all(const uint8_t *images, const mtb_layout_t &L, int tol, int ref, uint8_t *ws, int32_t *shifts_out,
             uint32_t *level_errs_out, int32_t *level_shifts_out, cudaStream_t s) {
     int rc = stage_pyramid(images, L, ws, s);
     if (rc != MTB_OK) return rc;
-    rc = cuda_status(launch_bitmaps(L, tol, ws, s));
+    rc = cuda_status(launch_bitmaps(L, tol, ws, s, true));
     if (rc != MTB_OK) return rc;
-    return stage_search(L, ref, ws, shifts_out, level_errs_out, level_shifts_out, s);
+    return cuda_status(launch_search(L, ref, ws, shifts_out, level_errs_out, level_shifts_out, s, true));
 }
 
 bool misaligned(const void *p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) != 0; }
@@ -208,7 +204,7 @@ int mtb_build_bitmaps(int n_exposures, int w, int h, int levels, int noise_tol, 
     if (noise_tol < 0 || noise_tol > 255) return MTB_ERR_INVALID_ARG;
     if (!workspace || workspace_bytes < L.total_bytes || misaligned(workspace, 256)) return MTB_ERR_INVALID_ARG;
     return cuda_status(launch_bitmaps(L, noise_tol, static_cast<uint8_t *>(workspace),
-                                      static_cast<cudaStream_t>(stream)));
+                                      static_cast<cudaStream_t>(stream), false));
 }
 
 int mtb_search_shifts(int n_exposures, int w, int h, int levels, int ref_idx, void *workspace,
@@ -219,8 +215,38 @@ int mtb_search_shifts(int n_exposures, int w, int h, int levels, int ref_idx, vo
     if (rc != MTB_OK) return rc;
     if (ref_idx < 0 || ref_idx >= n_exposures) return MTB_ERR_INVALID_ARG;
     if (!workspace || workspace_bytes < L.total_bytes || misaligned(workspace, 256)) return MTB_ERR_INVALID_ARG;
-    return stage_search(L, ref_idx, static_cast<uint8_t *>(workspace), shifts_out, level_errs_out,
-                        level_shifts_out, static_cast<cudaStream_t>(stream));
+    return cuda_status(launch_search(L, ref_idx, static_cast<uint8_t *>(workspace), shifts_out, level_errs_out,
+                                     level_shifts_out, static_cast<cudaStream_t>(stream), false));
+}
+
+int mtb_workspace_status(const void *workspace, size_t workspace_bytes, int n_exposures, int w, int h, int levels,
+                         void *stream) {
+    mtb_layout_t L;
+    int rc = compute_layout(n_exposures, w, h, levels, &L);
+    if (rc != MTB_OK) return rc;
+    if (!workspace || workspace_bytes < L.total_bytes || misaligned(workspace, 256)) return MTB_ERR_INVALID_ARG;
+    if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return MTB_ERR_CUDA;
+    int32_t status = 0;
+    if (cudaMemcpy(&status, static_cast<const uint8_t *>(workspace) + L.status_offset, sizeof(status),
+                   cudaMemcpyDeviceToHost) != cudaSuccess)
+        return MTB_ERR_CUDA;
+    return status;
+}
+
+int mtb_debug_search_withheld(int n_exposures, int w, int h, int levels, int ref_idx, void *workspace,
+                              size_t workspace_bytes, long long timeout_ns, void *stream) {
+    mtb_layout_t L;
+    int rc = compute_layout(n_exposures, w, h, levels, &L);
+    if (rc != MTB_OK) return rc;
+    if (ref_idx < 0 || ref_idx >= n_exposures || timeout_ns <= 0 || timeout_ns > 1000000000LL)
+        return MTB_ERR_INVALID_ARG;
+    if (!workspace || workspace_bytes < L.total_bytes || misaligned(workspace, 256)) return MTB_ERR_INVALID_ARG;
+    if (coarse_start_level(L) >= L.levels) return MTB_ERR_INVALID_ARG;  // no resolve item to withhold
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    rc = cuda_status(launch_search_ex(L, ref_idx, static_cast<uint8_t *>(workspace), nullptr, nullptr, nullptr, s,
+                                      false, (unsigned long long)timeout_ns, 0));
+    if (rc != MTB_OK) return rc;
+    return mtb_workspace_status(workspace, workspace_bytes, n_exposures, w, h, levels, stream);
 }
 
 size_t mtb_host_workspace_bytes(int n_exposures, int w, int h, int levels) {

@@ -1,72 +1,76 @@
-// mtb_bitmaps.cu -- median scan and bitmap packing.
+// mtb_bitmaps.cu -- threshold and exclusion bitmaps.
 //
-// Sec. III-A: the median of each pyramid image comes from its histogram, and the
-// median threshold bitmap (MTB) sets a pixel to 0 if it is <= the median, else 1.
-// Sec. III-B: the exclusion bitmap (EB) removes pixels within +-tol of the median.
-// Both maps are packed 1 bit per pixel (bit b of word q = pixel 32q + b) and
-// stored as (tb, eb) word pairs, so the search kernel fetches both with one
-// 8-byte load.  HBM traffic per pixel of a level: 1 byte read, 2 bits written.
+// Sec. III-A: the median threshold bitmap (MTB) sets a pixel to 0 if it is <=
+// the median of its pyramid image, else 1.  Sec. III-B: the exclusion bitmap
+// (EB) removes pixels within +-tol of the median.  Both maps are packed 1 bit
+// per pixel (bit b of word q = pixel 32q + b) and stored as (tb, eb) word pairs,
+// so the search fetches both with one 8-byte load.  HBM traffic per pixel of a
+// level: 1 byte read, 2 bits written.
 //
-// Levels deeper than the pyramid pass builds are small (at most 1/4096 of the
-// full-resolution pixels); one CTA per exposure builds them here from the
-// deepest tile level, with their histograms, medians and bitmaps.
-#include "mtb_internal.cuh"
+// The medians of levels 0..tile_levels-1 come from the pyramid pass.  Deeper
+// levels are small (at most 1/4096 of the full-resolution pixels): one CTA per
+// exposure builds them here from the deepest tile level, with their histograms,
+// medians and bitmaps.
+//
+// Comparisons run on 4 pixels at a time (SWAR on bytes): for a constant t,
+// the MSB of every byte of
+//     ge(x) = (x & ~T) | ((x ^ ~T) & ((x | 0x80..) - (T & 0x7f..)))
+// is [x_byte >= t]  (T = t in every byte; the subtraction cannot borrow across
+// bytes because each byte of the minuend is >= 0x80).  The 4 MSBs of a word are
+// gathered into 4 adjacent bits by one multiply: bits 7, 15, 23, 31 times
+// 2^21 + 2^14 + 2^7 + 1 land on bits 28..31 without carries.
+#include "mtb_device.cuh"
 
 namespace mtb {
 namespace {
 
-// Lower median (smallest v with cumulative count >= ceil(N/2)) of a 256-bin
-// histogram; called by all 32 lanes of one warp, returns the median to all.
-__device__ int warp_median(const uint32_t *hist) {
-    const unsigned full = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
-    uint32_t c[8];
-    uint32_t s = 0;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        c[k] = hist[lane * 8 + k];
-        s += c[k];
-    }
-    uint32_t inc = s;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t t = __shfl_up_sync(full, inc, o);
-        if (lane >= o) inc += t;
-    }
-    const uint32_t total = __shfl_sync(full, inc, 31);
-    const uint32_t half = total / 2 + (total & 1u);  // ceil(total / 2)
-    const uint32_t before = inc - s;
-    const unsigned owner_mask = __ballot_sync(full, half > before && half <= inc);
-    if (owner_mask == 0) return 0;
-    const int owner = __ffs(owner_mask) - 1;
-    int m = 0;
-    if (lane == owner) {
-        uint32_t cum = before;
-        m = lane * 8 + 7;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            cum += c[k];
-            if (cum >= half) {
-                m = lane * 8 + k;
-                break;
-            }
-        }
-    }
-    return __shfl_sync(full, m, owner);
-}
+constexpr uint32_t kHi = 0x80808080u;
+constexpr uint32_t kLo7 = 0x7f7f7f7fu;
 
-// tb and eb bits of 32 gray pixels held in 8 little-endian words; only the
-// first nvalid pixels can be set.
-__device__ __forceinline__ uint2 pack_bits(const uint32_t (&v)[8], int m, int tol, int nvalid) {
-    const int lo = m - tol;
-    const uint32_t band = 2u * (uint32_t)tol;
+// Per-byte x >= t test for a fixed t in [0, 255], result in each byte's MSB.
+struct ByteGE {
+    uint32_t t_lo7, not_t;
+    __device__ __forceinline__ explicit ByteGE(uint32_t t) {
+        const uint32_t T = t * 0x01010101u;
+        t_lo7 = T & kLo7;
+        not_t = ~T;
+    }
+    __device__ __forceinline__ uint32_t operator()(uint32_t x) const {
+        const uint32_t d = (x | kHi) - t_lo7;
+        return (x & not_t) | ((x ^ not_t) & d);
+    }
+};
+
+// The thresholds of one (exposure, level): tb = [g >= m + 1], eb = [g < lo] or
+// [g >= hi + 1]; a test that can never hold is masked out instead.
+struct Thresholds {
+    ByteGE tb, lo, hi;
+    uint32_t tb_mask, hi_mask;
+    __device__ __forceinline__ Thresholds(int m, int tol)
+        : tb((uint32_t)min(m + 1, 255)), lo((uint32_t)max(m - tol, 0)), hi((uint32_t)min(m + tol + 1, 255)),
+          tb_mask(m < 255 ? kHi : 0u), hi_mask(m + tol < 255 ? kHi : 0u) {}
+};
+
+// MSBs of bytes 0..3 of x (already masked to kHi) -> bits 0..3.
+__device__ __forceinline__ uint32_t msb_nibble_top(uint32_t x) { return x * 0x00204081u; }
+
+// tb and eb words of 32 gray pixels in 8 little-endian words; only the first
+// nvalid pixels can be set.
+__device__ __forceinline__ uint2 pack_bits(const uint32_t (&v)[8], const Thresholds &th, int nvalid) {
     uint32_t tb = 0, eb = 0;
 #pragma unroll
-    for (int b = 0; b < 32; ++b) {
-        const int g = (int)((v[b >> 2] >> ((b & 3) * 8)) & 0xffu);
-        tb |= (uint32_t)(g > m) << b;
-        // outside [m - tol, m + tol]  <=>  (g - lo) does not lie in [0, 2 tol]
-        eb |= (uint32_t)((uint32_t)(g - lo) > band) << b;
+    for (int k = 0; k < 8; ++k) {
+        const uint32_t tm = th.tb(v[k]) & th.tb_mask;
+        const uint32_t em = (~th.lo(v[k]) | (th.hi(v[k]) & th.hi_mask)) & kHi;
+        // top nibble of the product holds the 4 flags; move it to bits 4k..4k+3
+        const uint32_t pt = msb_nibble_top(tm), pe = msb_nibble_top(em);
+        if (k == 7) {
+            tb |= pt & 0xf0000000u;
+            eb |= pe & 0xf0000000u;
+        } else {
+            tb |= (pt >> (28 - 4 * k)) & (0xfu << (4 * k));
+            eb |= (pe >> (28 - 4 * k)) & (0xfu << (4 * k));
+        }
     }
     const uint32_t keep = nvalid >= 32 ? 0xffffffffu : ((1u << nvalid) - 1u);
     return make_uint2(tb & keep, eb & keep);
@@ -97,14 +101,14 @@ __device__ void deep_levels(const mtb_layout_t &L, uint8_t *ws, int tol, int e, 
         uint32_t *gh = Planes::hist(ws, L, e, l);
         for (int v = tid; v < 256; v += blockDim.x) gh[v] = s_hist[v];
         if (tid < 32) {
-            const int m = warp_median(s_hist);
+            const int m = warp_median<false>(s_hist);
             if (tid == 0) {
                 *s_med = m;
                 *Planes::median(ws, L, e, l) = m;
             }
         }
         __syncthreads();
-        const int m = *s_med;
+        const Thresholds th(*s_med, tol);
         const int bp = L.bits_pitch[l];
         uint2 *out = Planes::bits(ws, L, e, l);
         for (int idx = tid; idx < bp * Hl; idx += blockDim.x) {
@@ -115,7 +119,7 @@ __device__ void deep_levels(const mtb_layout_t &L, uint8_t *ws, int tol, int e, 
                 const uint4 *p = reinterpret_cast<const uint4 *>(dst + (size_t)y * gpl + x);
                 const uint4 a = __ldcg(p), b = __ldcg(p + 1);
                 const uint32_t v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-                r = pack_bits(v, m, tol, min(32, Wl - x));
+                r = pack_bits(v, th, min(32, Wl - x));
             }
             out[idx] = r;
         }
@@ -127,6 +131,8 @@ __global__ void __launch_bounds__(kBitThreads)
 k_bitmaps(const mtb_layout_t L, uint8_t *__restrict__ ws, int tol, int deep_ctas, int chunks_per_exp) {
     __shared__ uint32_t s_hist[256];
     __shared__ int s_med;
+    pdl_trigger();
+    pdl_wait();  // gray planes and medians come from the pyramid pass
     if ((int)blockIdx.x < deep_ctas) {
         deep_levels(L, ws, tol, blockIdx.x, s_hist, &s_med);
         return;
@@ -141,20 +147,15 @@ k_bitmaps(const mtb_layout_t L, uint8_t *__restrict__ ws, int tol, int deep_ctas
         if (c < ch) break;
         c -= ch;
     }
-    if (threadIdx.x < 32) {
-        const int m = warp_median(Planes::hist(ws, L, e, l));
-        if (threadIdx.x == 0) {
-            s_med = m;
-            if (c == 0) *Planes::median(ws, L, e, l) = m;
-        }
-    }
+    if (threadIdx.x == 0) s_med = *Planes::median(ws, L, e, l);
     __syncthreads();
-    const int m = s_med;
+    const Thresholds th(s_med, tol);
     const int Wl = L.width[l], Hl = L.height[l], bp = L.bits_pitch[l], gpl = L.gray_pitch[l];
     const uint8_t *g = Planes::gray(ws, L, e, l);
     uint2 *out = Planes::bits(ws, L, e, l);
     const int words = bp * Hl;
     const int w_end = min(words, (c + 1) * kBitWordsPerCta);
+#pragma unroll 4
     for (int idx = c * kBitWordsPerCta + threadIdx.x; idx < w_end; idx += kBitThreads) {
         const int y = idx / bp, q = idx - y * bp;
         const int x = q * 32;
@@ -163,7 +164,7 @@ k_bitmaps(const mtb_layout_t L, uint8_t *__restrict__ ws, int tol, int deep_ctas
             const uint4 *p = reinterpret_cast<const uint4 *>(g + (size_t)y * gpl + x);
             const uint4 a = __ldcs(p), b = __ldcs(p + 1);
             const uint32_t v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-            r = pack_bits(v, m, tol, min(32, Wl - x));
+            r = pack_bits(v, th, min(32, Wl - x));
         }
         out[idx] = r;
     }
@@ -171,7 +172,7 @@ k_bitmaps(const mtb_layout_t L, uint8_t *__restrict__ ws, int tol, int deep_ctas
 
 }  // namespace
 
-cudaError_t launch_bitmaps(const mtb_layout_t &L, int noise_tol, uint8_t *ws, cudaStream_t s) {
+cudaError_t launch_bitmaps(const mtb_layout_t &L, int noise_tol, uint8_t *ws, cudaStream_t s, bool chained) {
     long long per_exp = 0;
     for (int l = 0; l < L.tile_levels; ++l) {
         const long long words = (long long)L.bits_pitch[l] * L.height[l];
@@ -180,8 +181,8 @@ cudaError_t launch_bitmaps(const mtb_layout_t &L, int noise_tol, uint8_t *ws, cu
     const int deep = L.levels > L.tile_levels ? L.n : 0;
     const long long grid = deep + per_exp * L.n;
     if (grid > 0x7fffffffLL) return cudaErrorInvalidValue;
-    k_bitmaps<<<(unsigned)grid, kBitThreads, 0, s>>>(L, ws, noise_tol, deep, (int)per_exp);
-    return cudaGetLastError();
+    return launch_k(k_bitmaps, dim3((unsigned)grid), dim3(kBitThreads), s, chained, L, ws, noise_tol, deep,
+                    (int)per_exp);
 }
 
 }  // namespace mtb

@@ -1,0 +1,104 @@
+// mtb_device.cuh -- device helpers shared by the kernels of the library.
+#pragma once
+
+#include "mtb_internal.cuh"
+
+namespace mtb {
+
+// Lower median (smallest v with cumulative count >= ceil(N/2)) of a 256-bin
+// histogram in global memory (read through L2) or shared memory; called by all
+// 32 lanes of one warp, returns the median to all of them.
+template <bool kL2>
+__device__ __forceinline__ int warp_median(const uint32_t *hist) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    uint32_t c[8];
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        c[k] = kL2 ? __ldcg(hist + lane * 8 + k) : hist[lane * 8 + k];
+        s += c[k];
+    }
+    uint32_t inc = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(full, inc, o);
+        if (lane >= o) inc += t;
+    }
+    const uint32_t total = __shfl_sync(full, inc, 31);
+    const uint32_t half = total / 2 + (total & 1u);  // ceil(total / 2)
+    const uint32_t before = inc - s;
+    const unsigned owner_mask = __ballot_sync(full, half > before && half <= inc);
+    if (owner_mask == 0) return 0;
+    const int owner = __ffs(owner_mask) - 1;
+    int m = 0;
+    if (lane == owner) {
+        uint32_t cum = before;
+        m = lane * 8 + 7;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            cum += c[k];
+            if (cum >= half) {
+                m = lane * 8 + k;
+                break;
+            }
+        }
+    }
+    return __shfl_sync(full, m, owner);
+}
+
+// Programmatic dependent launch.  A kernel launched with
+// cudaLaunchAttributeProgrammaticStreamSerialization may start while the
+// previous kernel of the stream still runs; pdl_wait() blocks until that kernel
+// has finished and its writes are visible (a no-op without the attribute), and
+// pdl_trigger() lets the next kernel start launching.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+__device__ __forceinline__ int32_t *counters(uint8_t *ws, const mtb_layout_t &L) {
+    return reinterpret_cast<int32_t *>(ws + L.counter_offset);
+}
+
+// Counter area: [0, n) pyramid tiles finished per exposure; n + kCtrQueue the
+// search's work-queue head; from n + kCtrDone, done[pair][level] (chunks of a
+// level of a pair finished), then brute[pair] (window rows of a pair's coarse
+// levels finished).
+enum CounterSlot { kCtrQueue = 0, kCtrDone = 8 };
+
+__device__ __forceinline__ int32_t *status_word(uint8_t *ws, const mtb_layout_t &L) {
+    return reinterpret_cast<int32_t *>(ws + L.status_offset);
+}
+
+__device__ __forceinline__ unsigned long long global_timer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ int ld_acquire(const int32_t *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Spins (thread-level) until *ctr >= target.  Gives up when *status is already
+// set by another wait, or after timeout_ns, in which case it sets *status to
+// MTB_ERR_TIMEOUT.  Returns true if the target was reached.
+__device__ __forceinline__ bool wait_at_least(const int32_t *ctr, int target, int32_t *status,
+                                              unsigned long long timeout_ns) {
+    if (ld_acquire(ctr) >= target) return true;
+    const unsigned long long deadline = global_timer_ns() + timeout_ns;
+    unsigned ns = 32;
+    for (;;) {
+        __nanosleep(ns);
+        if (ns < 1024) ns <<= 1;
+        if (ld_acquire(ctr) >= target) return true;
+        if (ld_acquire(status) != 0) return false;
+        if (global_timer_ns() > deadline) {
+            atomicCAS(status, 0, MTB_ERR_TIMEOUT);
+            return false;
+        }
+    }
+}
+
+}  // namespace mtb

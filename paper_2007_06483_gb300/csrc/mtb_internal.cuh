@@ -25,9 +25,23 @@ constexpr int kGroupsPerRow = kTileCols / 16 + 1;  // 16-pixel groups touching o
 // Bitmap pass: one CTA turns kBitWordsPerCta output words (32 pixels each) of
 // one (exposure, level) plane into bits.
 constexpr int kBitThreads = 256;
-constexpr int kBitWordsPerCta = 2048;
+constexpr int kBitWordsPerCta = 1024;
 
 constexpr int kMaxShiftThreads = 256;
+
+// Coarse search levels: from the deepest level up, every level whose whole
+// reachable window (radius R = 2^(levels - l) - 1 <= kMaxTableRadius) costs at
+// most kBruteBudget word-candidate evaluations per pair is searched by brute
+// force over that window; the coarse-to-fine chain through those levels is
+// then walked in the resulting error tables (kTableWords per pair: the windows
+// of radius 1, 3, 7 and 15 take 9 + 49 + 225 + 961 = 1244 words).
+constexpr int kMaxTableRadius = 15;
+constexpr long long kBruteBudget = 8ll << 20;
+constexpr int kTableWords = 1280;
+
+// Bound on any device-side wait of the search (the waits always end when the
+// kernels are correct; the bound turns a bug into MTB_ERR_TIMEOUT, not a hang).
+constexpr unsigned long long kSearchTimeoutNs = 2000000000ull;
 
 // ---------------------------------------------------------------------------
 // Readings of the paper's unstated points, restated for the device.
@@ -84,11 +98,39 @@ struct Planes {
 int compute_layout(int n, int w, int h, int levels, mtb_layout_t *L);
 int check_stack_args(int n, int w, int h, int levels, int noise_tol, int ref_idx);
 
+// `chained`: the launch directly follows this library's previous stage in the
+// same call, so its first kernel may overlap that stage's tail (programmatic
+// dependent launch).  A stage called on its own starts after all earlier work.
 cudaError_t launch_pyramid(const uint8_t *images, const mtb_layout_t &L, uint8_t *ws, cudaStream_t s);
-cudaError_t launch_bitmaps(const mtb_layout_t &L, int noise_tol, uint8_t *ws, cudaStream_t s);
+cudaError_t launch_bitmaps(const mtb_layout_t &L, int noise_tol, uint8_t *ws, cudaStream_t s, bool chained);
+int coarse_start_level(const mtb_layout_t &L);
 cudaError_t launch_search(const mtb_layout_t &L, int ref_idx, uint8_t *ws, int32_t *shifts_out,
-                          uint32_t *level_errs_out, int32_t *level_shifts_out, cudaStream_t s);
+                          uint32_t *level_errs_out, int32_t *level_shifts_out, cudaStream_t s, bool chained);
+cudaError_t launch_search_ex(const mtb_layout_t &L, int ref_idx, uint8_t *ws, int32_t *shifts_out,
+                             uint32_t *level_errs_out, int32_t *level_shifts_out, cudaStream_t s, bool chained,
+                             unsigned long long timeout_ns, int withhold_pair);
 
 int device_sm_count();
+
+// Launches kernel<<<grid, block, 0, s>>>(args...).  With `after_previous` the
+// launch carries the programmatic-stream-serialization attribute: it may begin
+// while the previous kernel in the stream runs, and the kernel orders its
+// dependent accesses with pdl_wait().  The first kernel of a call is launched
+// without it, so it starts only after all earlier work in the stream.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, bool after_previous,
+                     Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = after_previous ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
 
 }  // namespace mtb

@@ -2,15 +2,23 @@
 //
 // One read of the interleaved RGB8 exposures produces, for every exposure:
 //   * the gray image (Sec. III-A: exposures are converted to gray-scale),
-//   * pyramid levels 1..tile_levels-1 (Sec. III-A: halve both dimensions, the
-//     next level made from the previous one, Sec. III-B),
-//   * the 256-bin histogram of each of those levels (Sec. III-B).
-// The CTA owns a 32-row x 256-column tile of full-resolution pixels.  Level l
-// pixels of the tile have their whole 2^l x 2^l source block inside the tile
-// (l <= 5), so the tile's part of levels 1..5 is built in shared memory from
-// the gray tile without touching HBM again.  HBM traffic per full-resolution
-// pixel: 3 bytes read (RGB) + 4/3 bytes written (gray levels).
-#include "mtb_internal.cuh"
+//   * pyramid levels 1..tile_levels-1 (Sec. III-A: halve both dimensions, each
+//     level made from the previous one as in Sec. III-B),
+//   * the 256-bin histogram of each of those levels and its median (Sec. III-A,
+//     Sec. III-B).
+// A CTA owns 32-row x 256-column tiles of full-resolution pixels.  Level-l
+// pixels of a tile have their whole 2^l x 2^l source block inside it (l <= 5),
+// so the tile's part of levels 1..5 is built in shared memory from the gray
+// tile.  HBM traffic per full-resolution pixel: 3 bytes read (RGB) + 4/3 bytes
+// written (gray levels).
+//
+// Instruction budget: at HBM speed the pass has about 17 thread-instructions per
+// pixel, so the gray conversion uses two byte dot products (dp4a) per pixel on
+// byte-permuted RGB words, gray is packed with byte permutes, the 2x2 shrink is
+// done on 16-bit lanes, and a 16-pixel group of one value adds to the histogram
+// with a single shared atomic (saturated regions would otherwise serialise 32
+// lanes on one bin).
+#include "mtb_device.cuh"
 
 namespace mtb {
 namespace {
@@ -23,192 +31,353 @@ __host__ __device__ constexpr int lv_offset(int l) {
 }
 constexpr int kLvBytes = lv_offset(kTileLog2 + 1);
 
-__device__ __forceinline__ uint32_t byte_of(const uint32_t (&w)[12], int k) {
-    return (w[k >> 2] >> ((k & 3) * 8)) & 0xffu;
+struct PyrShared {
+    alignas(16) uint8_t lv[kLvBytes];
+    uint32_t h01[2][kPyrWarps][256];  // warp-private, levels 0 and 1
+    uint32_t hs[kTileLog2 - 1][256];  // levels 2..5, one per CTA
+    int last;
+};
+
+// Q14 luma weights split into high and low bytes: w = 256 * hi + lo, so two
+// byte dot products give the weighted sum exactly.
+constexpr uint32_t kWHi = 19u | (37u << 8) | (7u << 16);
+constexpr uint32_t kWLo = 35u | (145u << 8) | (76u << 16);
+static_assert(19 * 256 + 35 == 4899 && 37 * 256 + 145 == 9617 && 7 * 256 + 76 == 1868, "Q14 weight split");
+
+// Gray of the pixel whose R, G, B are bytes 0..2 (lo3) or 1..3 (hi3) of a word.
+__device__ __forceinline__ uint32_t luma_lo3(uint32_t w) {
+    return (__dp4a(w, kWHi, 0u) * 256u + __dp4a(w, kWLo, 8192u)) >> 14;
+}
+__device__ __forceinline__ uint32_t luma_hi3(uint32_t w) {
+    return (__dp4a(w, kWHi << 8, 0u) * 256u + __dp4a(w, kWLo << 8, 8192u)) >> 14;
 }
 
-// Gray values of the 16 pixels starting at flat pixel index gp (a multiple of
-// 16, so the 48 RGB bytes are one 16-byte aligned run).  Pixels at or past
-// total_px (only in the last group of the buffer) are read one byte at a time
-// and left 0.
-__device__ __forceinline__ void gray_group(const uint8_t *__restrict__ images, uint64_t gp,
-                                           uint64_t total_px, uint32_t (&g)[16]) {
-    if (gp + 16 <= total_px) {
-        const uint4 *src = reinterpret_cast<const uint4 *>(images + 3 * gp);
-        const uint4 a = __ldcs(src), b = __ldcs(src + 1), c = __ldcs(src + 2);
-        const uint32_t w[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
+// 4 pixels = 12 RGB bytes in words w0..w2 -> their gray values and the packed word.
+__device__ __forceinline__ uint32_t gray4(uint32_t w0, uint32_t w1, uint32_t w2, uint32_t *g) {
+    g[0] = luma_lo3(w0);
+    g[1] = luma_lo3(__byte_perm(w0, w1, 0x0543));  // bytes 3, 4, 5
+    g[2] = luma_lo3(__byte_perm(w1, w2, 0x0432));  // bytes 6, 7, 8
+    g[3] = luma_hi3(w2);                          // bytes 9, 10, 11
+    return __byte_perm(__byte_perm(g[0], g[1], 0x3340), __byte_perm(g[2], g[3], 0x3340), 0x5410);
+}
+
+// 16 pixels of one 48-byte group -> gray values and 4 packed words.
+__device__ __forceinline__ uint4 gray16(const uint4 &a, const uint4 &b, const uint4 &c, uint32_t (&g)[16]) {
+    uint4 v;
+    v.x = gray4(a.x, a.y, a.z, g + 0);
+    v.y = gray4(a.w, b.x, b.y, g + 4);
+    v.z = gray4(b.z, b.w, c.x, g + 8);
+    v.w = gray4(c.y, c.z, c.w, g + 12);
+    return v;
+}
+
+// Histogram of a group's pixels q in [qa, qb); one atomic if all 16 are equal.
+__device__ __forceinline__ void hist_group(uint32_t *h, const uint32_t (&g)[16], const uint4 &v, int qa, int qb) {
+    const uint32_t b0 = __byte_perm(v.x, 0u, 0x0000u);
+    if (qa == 0 && qb == 16 && v.x == b0 && v.y == b0 && v.z == b0 && v.w == b0) {
+        atomicAdd(h + g[0], 16u);
+        return;
+    }
 #pragma unroll
-        for (int q = 0; q < 16; ++q) g[q] = luma(byte_of(w, 3 * q), byte_of(w, 3 * q + 1), byte_of(w, 3 * q + 2));
-    } else {
+    for (int q = 0; q < 16; ++q)
+        if (q >= qa && q < qb) atomicAdd(h + g[q], 1u);
+}
+
+// Two shrunk pixels (16-bit lanes) from 4 pixels of each of two rows.
+__device__ __forceinline__ uint32_t shrink2(uint32_t a, uint32_t b) {
+    const uint32_t s = __byte_perm(a, 0u, 0x4240u) + __byte_perm(a, 0u, 0x4341u) + __byte_perm(b, 0u, 0x4240u) +
+                       __byte_perm(b, 0u, 0x4341u) + 0x00020002u;
+    return (s >> 2) & 0x00ff00ffu;
+}
+
+// ---- level 0 of one tile: gray into shared memory (and global), histogram ----
+// W is a multiple of 16: every tile row is a whole number of aligned groups.
+__device__ __forceinline__ void tile_level0_aligned(const uint8_t *__restrict__ images, const mtb_layout_t &L,
+                                                    uint8_t *ws, int e, int y0, int x0, int rows, int cols,
+                                                    PyrShared &sm) {
+    const int tid = threadIdx.x;
+    const uint64_t W = (uint64_t)L.w;
+    const uint64_t e0 = (uint64_t)e * W * (uint64_t)L.h;
+    uint8_t *g0 = Planes::gray(ws, L, e, 0);
+    const size_t gp0 = (size_t)L.gray_pitch[0];
+    uint32_t *h0 = sm.h01[0][tid >> 5];
+    constexpr int kGroups = kTileRows * (kTileCols / 16);
+    constexpr int kPer = kGroups / kPyrThreads;
+    uint4 raw[kPer][3];
+    bool ok[kPer];
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-            g[q] = 0;
-            if (gp + q < total_px) {
-                const uint8_t *p = images + 3 * (gp + q);
-                g[q] = luma(p[0], p[1], p[2]);
-            }
+    for (int k = 0; k < kPer; ++k) {
+        const int grp = tid + k * kPyrThreads;
+        const int r = grp >> 4, c = (grp & 15) << 4;
+        ok[k] = r < rows && c < cols;
+        if (ok[k]) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(images + 3 * (e0 + (uint64_t)(y0 + r) * W + x0 + c));
+            raw[k][0] = __ldcs(src);
+            raw[k][1] = __ldcs(src + 1);
+            raw[k][2] = __ldcs(src + 2);
         }
+    }
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        if (!ok[k]) continue;
+        const int grp = tid + k * kPyrThreads;
+        const int r = grp >> 4, c = (grp & 15) << 4;
+        uint32_t g[16];
+        const uint4 v = gray16(raw[k][0], raw[k][1], raw[k][2], g);
+        *reinterpret_cast<uint4 *>(sm.lv + r * kTileCols + c) = v;
+        *reinterpret_cast<uint4 *>(g0 + (size_t)(y0 + r) * gp0 + x0 + c) = v;
+        hist_group(h0, g, v, 0, 16);
     }
 }
 
-__global__ void __launch_bounds__(kPyrThreads)
-k_pyramid(const uint8_t *__restrict__ images, const mtb_layout_t L, uint8_t *__restrict__ ws,
-          int tiles_x, int tiles_per_exp, int total_tiles) {
-    __shared__ __align__(16) uint8_t s_lv[kLvBytes];
-    __shared__ uint32_t s_h01[2][kPyrWarps][256];    // warp-private, levels 0 and 1
-    __shared__ uint32_t s_hs[kTileLog2 - 1][256];     // levels 2..5, one per CTA
-
+// Any W: the tile row's pixels are a flat run [p0, p0 + cols) that starts
+// anywhere inside a 16-pixel group, so groups are clipped to it.
+__device__ __forceinline__ void tile_level0_general(const uint8_t *__restrict__ images, const mtb_layout_t &L,
+                                                    uint8_t *ws, int e, int y0, int x0, int rows, int cols,
+                                                    PyrShared &sm) {
     const int tid = threadIdx.x;
-    const int warp = tid >> 5;
-    const int K = L.tile_levels - 1;
-    const int W = L.w, H = L.h;
-    const uint64_t plane_px = (uint64_t)W * H;
-    const uint64_t total_px = plane_px * L.n;
-
-    for (int v = tid; v < 2 * kPyrWarps * 256; v += kPyrThreads) (&s_h01[0][0][0])[v] = 0;
-    for (int v = tid; v < (kTileLog2 - 1) * 256; v += kPyrThreads) (&s_hs[0][0])[v] = 0;
-
-    // Adds this CTA's histograms of exposure e to the global ones and clears them.
-    auto flush = [&](int e) {
-        __syncthreads();
-        for (int l = 0; l <= K; ++l) {
-            uint32_t *gh = Planes::hist(ws, L, e, l);
-            for (int v = tid; v < 256; v += kPyrThreads) {
-                uint32_t sum = 0;
-                if (l <= 1) {
+    const uint64_t W = (uint64_t)L.w;
+    const uint64_t plane_px = W * (uint64_t)L.h;
+    const uint64_t total_px = plane_px * (uint64_t)L.n;
+    const uint64_t e0 = (uint64_t)e * plane_px;
+    uint32_t *h0 = sm.h01[0][tid >> 5];
+    for (int s = tid; s < kTileRows * kGroupsPerRow; s += kPyrThreads) {
+        const int r = s / kGroupsPerRow;
+        const int j = s - r * kGroupsPerRow;
+        if (r >= rows) continue;
+        const uint64_t p0 = e0 + (uint64_t)(y0 + r) * W + x0;
+        const uint64_t gp = ((p0 >> 4) + j) << 4;
+        if (gp >= p0 + cols) continue;
+        uint32_t g[16];
+        uint4 v;
+        if (gp + 16 <= total_px) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(images + 3 * gp);
+            v = gray16(__ldcs(src), __ldcs(src + 1), __ldcs(src + 2), g);
+        } else {  // the buffer's last group: pixels past its end are not read
 #pragma unroll
-                    for (int w = 0; w < kPyrWarps; ++w) {
-                        sum += s_h01[l][w][v];
-                        s_h01[l][w][v] = 0;
-                    }
-                } else {
-                    sum = s_hs[l - 2][v];
-                    s_hs[l - 2][v] = 0;
+            for (int q = 0; q < 16; ++q) {
+                g[q] = 0;
+                if (gp + q < total_px) {
+                    const uint8_t *p = images + 3 * (gp + q);
+                    g[q] = luma(p[0], p[1], p[2]);
                 }
-                if (sum) atomicAdd(gh + v, sum);
+            }
+            v.x = g[0] | (g[1] << 8) | (g[2] << 16) | (g[3] << 24);
+            v.y = g[4] | (g[5] << 8) | (g[6] << 16) | (g[7] << 24);
+            v.z = g[8] | (g[9] << 8) | (g[10] << 16) | (g[11] << 24);
+            v.w = g[12] | (g[13] << 8) | (g[14] << 16) | (g[15] << 24);
+        }
+        const int c0 = (int)((int64_t)gp - (int64_t)p0);  // tile column of pixel 0 of the group; may be < 0
+        const int qa = max(0, -c0), qb = min(16, cols - c0);
+        uint8_t *row = sm.lv + r * kTileCols;
+        if (qa == 0 && qb == 16 && (c0 & 15) == 0) {
+            *reinterpret_cast<uint4 *>(row + c0) = v;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 16; ++q)
+                if (q >= qa && q < qb) row[c0 + q] = (uint8_t)g[q];
+        }
+        hist_group(h0, g, v, qa, qb);
+    }
+}
+
+// Level 0 of the tile from shared memory to global (16-byte stores); used when
+// the level-0 groups were clipped and written byte by byte.
+__device__ __forceinline__ void tile_store_level0(const mtb_layout_t &L, uint8_t *ws, int e, int y0, int x0,
+                                                  int rows, int cols, const PyrShared &sm) {
+    uint8_t *g0 = Planes::gray(ws, L, e, 0);
+    const size_t gp0 = (size_t)L.gray_pitch[0];
+    for (int s = threadIdx.x; s < kTileRows * (kTileCols / 16); s += kPyrThreads) {
+        const int r = s >> 4;
+        const int c = (s & 15) << 4;
+        if (r < rows && c < cols)
+            *reinterpret_cast<uint4 *>(g0 + (size_t)(y0 + r) * gp0 + x0 + c) =
+                *reinterpret_cast<const uint4 *>(sm.lv + r * kTileCols + c);
+    }
+}
+
+// ---- levels 1 and 2 of one tile in one pass ----
+// Thread u takes level-2 pixels (r2, c2..c2+1): level-1 pixels rows 2r2, 2r2+1,
+// columns 2c2..2c2+3, from level-0 rows 4r2..4r2+3, columns 4c2..4c2+7.  Level 1
+// goes to global only; level 2 also to shared memory for levels 3..5.
+__device__ __forceinline__ void tile_levels12(const mtb_layout_t &L, uint8_t *ws, int e, int y0, int x0, int K,
+                                              PyrShared &sm) {
+    static_assert((kTileRows / 4) * (kTileCols / 8) == kPyrThreads, "one level-2 pixel pair per thread");
+    const int u = threadIdx.x;
+    const int r2 = u / (kTileCols / 8), c2 = (u % (kTileCols / 8)) * 2;
+    const uint8_t *src = sm.lv + (4 * r2) * kTileCols + 4 * c2;
+    const uint2 a0 = *reinterpret_cast<const uint2 *>(src);
+    const uint2 a1 = *reinterpret_cast<const uint2 *>(src + kTileCols);
+    const uint2 a2 = *reinterpret_cast<const uint2 *>(src + 2 * kTileCols);
+    const uint2 a3 = *reinterpret_cast<const uint2 *>(src + 3 * kTileCols);
+    const uint32_t w1a = __byte_perm(shrink2(a0.x, a1.x), shrink2(a0.y, a1.y), 0x6420u);  // level-1 row 2r2
+    const uint32_t w1b = __byte_perm(shrink2(a2.x, a3.x), shrink2(a2.y, a3.y), 0x6420u);  // level-1 row 2r2+1
+    {
+        const int W1 = L.width[1], H1 = L.height[1];
+        const int gp1 = L.gray_pitch[1];
+        uint8_t *g1 = Planes::gray(ws, L, e, 1);
+        uint32_t *h1 = sm.h01[1][threadIdx.x >> 5];
+        const int xl = (x0 >> 1) + 2 * c2;
+#pragma unroll
+        for (int rr = 0; rr < 2; ++rr) {
+            const int yl = (y0 >> 1) + 2 * r2 + rr;
+            const uint32_t w = rr ? w1b : w1a;
+            if (yl < H1) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (xl + q < W1) atomicAdd(h1 + ((w >> (8 * q)) & 0xffu), 1u);
+                if (xl < gp1) *reinterpret_cast<uint32_t *>(g1 + (size_t)yl * gp1 + xl) = w;
             }
         }
-        __syncthreads();
-    };
+    }
+    if (K < 2) return;
+    const uint32_t p2 = shrink2(w1a, w1b);                     // [p0, 0, p1, 0] bytes
+    const uint16_t w2 = (uint16_t)__byte_perm(p2, 0u, 0x4420u);  // p0 | p1 << 8
+    *reinterpret_cast<uint16_t *>(sm.lv + lv_offset(2) + r2 * (kTileCols >> 2) + c2) = w2;
+    const int W2 = L.width[2], H2 = L.height[2];
+    const int gp2 = L.gray_pitch[2];
+    const int yl = (y0 >> 2) + r2, xl = (x0 >> 2) + c2;
+    if (yl < H2) {
+        if (xl < W2) atomicAdd(sm.hs[0] + (w2 & 0xffu), 1u);
+        if (xl + 1 < W2) atomicAdd(sm.hs[0] + (w2 >> 8), 1u);
+        if (xl < gp2) *reinterpret_cast<uint16_t *>(Planes::gray(ws, L, e, 2) + (size_t)yl * gp2 + xl) = w2;
+    }
+}
 
-    const int t0 = (int)(((long long)blockIdx.x * total_tiles) / gridDim.x);
-    const int t1 = (int)(((long long)(blockIdx.x + 1) * total_tiles) / gridDim.x);
-    int cur_e = t0 < t1 ? t0 / tiles_per_exp : -1;
+// ---- levels 3..K of one tile, by one warp, from level 2 in shared memory ----
+__device__ __forceinline__ void tile_levels_tail(const mtb_layout_t &L, uint8_t *ws, int e, int y0, int x0, int K,
+                                                 PyrShared &sm) {
+    const int lane = threadIdx.x & 31;
+    for (int l = 3; l <= K; ++l) {
+        const uint8_t *prev = sm.lv + lv_offset(l - 1);
+        const int ppitch = kTileCols >> (l - 1);
+        uint8_t *cur = sm.lv + lv_offset(l);
+        const int cpitch = kTileCols >> l;
+        const int upr = cpitch >> 2;  // 4-pixel units per row
+        const int units = (kTileRows >> l) * upr;
+        const int yl0 = y0 >> l, xl0 = x0 >> l;
+        const int Wl = L.width[l], Hl = L.height[l];
+        const int gpl = L.gray_pitch[l];
+        uint32_t *hl = sm.hs[l - 2];
+        for (int u = lane; u < units; u += 32) {
+            const int r = u / upr;
+            const int c = (u - r * upr) << 2;
+            const uint2 a = *reinterpret_cast<const uint2 *>(prev + (2 * r) * ppitch + 2 * c);
+            const uint2 b = *reinterpret_cast<const uint2 *>(prev + (2 * r + 1) * ppitch + 2 * c);
+            const uint32_t out = __byte_perm(shrink2(a.x, b.x), shrink2(a.y, b.y), 0x6420u);
+            *reinterpret_cast<uint32_t *>(cur + r * cpitch + c) = out;
+            const int yl = yl0 + r, xl = xl0 + c;
+            if (yl < Hl) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (xl + q < Wl) atomicAdd(hl + ((out >> (8 * q)) & 0xffu), 1u);
+                if (xl < gpl) *reinterpret_cast<uint32_t *>(Planes::gray(ws, L, e, l) + (size_t)yl * gpl + xl) = out;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// Adds the CTA's histograms of exposure e to the global ones, clears them and
+// counts the CTA's ntiles tiles of e as done.  The CTA that completes the
+// exposure's last tile computes the medians of levels 0..K (Sec. III-A).
+__device__ void flush_exposure(const mtb_layout_t &L, uint8_t *ws, int e, int ntiles, int tiles_per_exp, int K,
+                               PyrShared &sm) {
+    const int tid = threadIdx.x;
+    __syncthreads();
+    for (int l = 0; l <= K; ++l) {
+        uint32_t *gh = Planes::hist(ws, L, e, l);
+        const int v = tid;  // kPyrThreads == 256 bins
+        uint32_t sum = 0;
+        if (l <= 1) {
+#pragma unroll
+            for (int w = 0; w < kPyrWarps; ++w) {
+                sum += sm.h01[l][w][v];
+                sm.h01[l][w][v] = 0;
+            }
+        } else {
+            sum = sm.hs[l - 2][v];
+            sm.hs[l - 2][v] = 0;
+        }
+        if (sum) atomicAdd(gh + v, sum);
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+        const int old = atomicAdd(counters(ws, L) + e, ntiles);
+        sm.last = old + ntiles == tiles_per_exp;
+    }
+    __syncthreads();
+    if (sm.last) {
+        __threadfence();
+        const int warp = tid >> 5;
+        if (warp <= K) {
+            const int m = warp_median<true>(Planes::hist(ws, L, e, warp));
+            if ((tid & 31) == 0) *Planes::median(ws, L, e, warp) = m;
+        }
+    }
+    __syncthreads();
+}
+
+template <bool kAligned>
+__global__ void __launch_bounds__(kPyrThreads, 4)
+k_pyramid(const uint8_t *__restrict__ images, const mtb_layout_t L, uint8_t *__restrict__ ws, int tiles_x,
+          int tiles_per_exp, int total_tiles) {
+    static_assert(kPyrThreads == 256, "one thread per histogram bin in the flush");
+    __shared__ PyrShared sm;
+    const int tid = threadIdx.x;
+    const int K = L.tile_levels - 1;
+    for (int v = tid; v < 2 * kPyrWarps * 256; v += kPyrThreads) (&sm.h01[0][0][0])[v] = 0;
+    for (int v = tid; v < (kTileLog2 - 1) * 256; v += kPyrThreads) (&sm.hs[0][0])[v] = 0;
     __syncthreads();
 
+    pdl_trigger();
+    const int t0 = (int)(((long long)blockIdx.x * total_tiles) / gridDim.x);
+    const int t1 = (int)(((long long)(blockIdx.x + 1) * total_tiles) / gridDim.x);
+    int cur_e = -1, done = 0;
+    bool waited = false;
     for (int t = t0; t < t1; ++t) {
         const int e = t / tiles_per_exp;
         if (e != cur_e) {
-            flush(cur_e);
+            if (cur_e >= 0) {
+                if (!waited) pdl_wait();  // the histograms were cleared by the previous kernel
+                waited = true;
+                flush_exposure(L, ws, cur_e, done, tiles_per_exp, K, sm);
+            }
             cur_e = e;
+            done = 0;
         }
         const int rt = t - e * tiles_per_exp;
         const int ty = rt / tiles_x;
         const int tx = rt - ty * tiles_x;
         const int y0 = ty * kTileRows, x0 = tx * kTileCols;
-        const int rows = min(kTileRows, H - y0);
-        const int cols = min(kTileCols, W - x0);
-        const uint64_t e0 = (uint64_t)e * plane_px;
-
-        // ---- gray of level 0 into shared memory, histogram of level 0 ----
-        uint32_t *h0 = s_h01[0][warp];
-        for (int s = tid; s < kTileRows * kGroupsPerRow; s += kPyrThreads) {
-            const int r = s / kGroupsPerRow;
-            const int j = s - r * kGroupsPerRow;
-            if (r >= rows) continue;
-            const uint64_t p0 = e0 + (uint64_t)(y0 + r) * W + x0;  // first pixel of the row's span
-            const uint64_t gp = ((p0 >> 4) + j) << 4;
-            if (gp >= p0 + cols) continue;
-            uint32_t g[16];
-            gray_group(images, gp, total_px, g);
-            const int c0 = (int)((int64_t)gp - (int64_t)p0);  // tile column of g[0]; may be < 0
-            const int qa = max(0, -c0), qb = min(16, cols - c0);
-            uint8_t *row = s_lv + r * kTileCols;
-            if (qa == 0 && qb == 16 && (c0 & 15) == 0) {
-                uint4 v;
-                v.x = g[0] | (g[1] << 8) | (g[2] << 16) | (g[3] << 24);
-                v.y = g[4] | (g[5] << 8) | (g[6] << 16) | (g[7] << 24);
-                v.z = g[8] | (g[9] << 8) | (g[10] << 16) | (g[11] << 24);
-                v.w = g[12] | (g[13] << 8) | (g[14] << 16) | (g[15] << 24);
-                *reinterpret_cast<uint4 *>(row + c0) = v;
-            } else {
-#pragma unroll
-                for (int q = 0; q < 16; ++q)
-                    if (q >= qa && q < qb) row[c0 + q] = (uint8_t)g[q];
-            }
-            // runs of equal values go in with one shared-memory atomic each
-            uint32_t run_v = 0xffffffffu, run_n = 0;
-#pragma unroll
-            for (int q = 0; q < 16; ++q) {
-                if (q < qa || q >= qb) continue;
-                if (g[q] == run_v) {
-                    ++run_n;
-                } else {
-                    if (run_n) atomicAdd(h0 + run_v, run_n);
-                    run_v = g[q];
-                    run_n = 1;
-                }
-            }
-            if (run_n) atomicAdd(h0 + run_v, run_n);
-        }
+        const int rows = min(kTileRows, L.h - y0);
+        const int cols = min(kTileCols, L.w - x0);
+        if (kAligned)
+            tile_level0_aligned(images, L, ws, e, y0, x0, rows, cols, sm);
+        else
+            tile_level0_general(images, L, ws, e, y0, x0, rows, cols, sm);
         __syncthreads();
-
-        // ---- level 0 to global (16-byte stores) ----
-        {
-            uint8_t *g0 = Planes::gray(ws, L, e, 0);
-            const int gp0 = L.gray_pitch[0];
-            for (int s = tid; s < kTileRows * (kTileCols / 16); s += kPyrThreads) {
-                const int r = s / (kTileCols / 16);
-                const int c = (s - r * (kTileCols / 16)) * 16;
-                if (r < rows && c < cols)
-                    *reinterpret_cast<uint4 *>(g0 + (size_t)(y0 + r) * gp0 + x0 + c) =
-                        *reinterpret_cast<const uint4 *>(s_lv + r * kTileCols + c);
-            }
-        }
-
-        // ---- levels 1..K from the previous level in shared memory ----
-        for (int l = 1; l <= K; ++l) {
-            const uint8_t *prev = s_lv + lv_offset(l - 1);
-            const int ppitch = kTileCols >> (l - 1);
-            uint8_t *cur = s_lv + lv_offset(l);
-            const int cpitch = kTileCols >> l;
-            const int upr = cpitch >> 2;  // 4-pixel units per row
-            const int units = (kTileRows >> l) * upr;
-            const int yl0 = y0 >> l, xl0 = x0 >> l;
-            const int Wl = L.width[l], Hl = L.height[l], gpl = L.gray_pitch[l];
-            uint8_t *gl = Planes::gray(ws, L, e, l);
-            uint32_t *hl = l == 1 ? s_h01[1][warp] : s_hs[l - 2];
-            for (int u = tid; u < units; u += kPyrThreads) {
-                const int r = u / upr;
-                const int c = (u - r * upr) << 2;
-                const uint2 a = *reinterpret_cast<const uint2 *>(prev + (2 * r) * ppitch + 2 * c);
-                const uint2 b = *reinterpret_cast<const uint2 *>(prev + (2 * r + 1) * ppitch + 2 * c);
-                uint32_t out = 0;
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const uint32_t ta = q < 2 ? a.x : a.y, tb = q < 2 ? b.x : b.y;
-                    const int sh = (q & 1) * 16;
-                    const uint32_t v = box2((ta >> sh) & 0xffu, (ta >> (sh + 8)) & 0xffu,
-                                            (tb >> sh) & 0xffu, (tb >> (sh + 8)) & 0xffu);
-                    out |= v << (8 * q);
-                }
-                *reinterpret_cast<uint32_t *>(cur + r * cpitch + c) = out;
-                const int yl = yl0 + r, xl = xl0 + c;
-                if (yl < Hl) {
-#pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        if (xl + q < Wl) atomicAdd(hl + ((out >> (8 * q)) & 0xffu), 1u);
-                    if (xl < gpl) *reinterpret_cast<uint32_t *>(gl + (size_t)yl * gpl + xl) = out;
-                }
-            }
-            __syncthreads();
-        }
-        if (K == 0) __syncthreads();
+        if (!kAligned) tile_store_level0(L, ws, e, y0, x0, rows, cols, sm);
+        if (K >= 1) tile_levels12(L, ws, e, y0, x0, K, sm);
+        __syncthreads();
+        // levels 3..5 by one warp (a different one per tile) while the others
+        // start the next tile, which only writes level 0 of the shared buffer
+        if (K >= 3 && (tid >> 5) == (t & (kPyrWarps - 1))) tile_levels_tail(L, ws, e, y0, x0, K, sm);
+        ++done;
     }
-    if (cur_e >= 0) flush(cur_e);
+    if (cur_e >= 0) {
+        if (!waited) pdl_wait();
+        flush_exposure(L, ws, cur_e, done, tiles_per_exp, K, sm);
+    }
 }
 
-int g_pyr_blocks_per_sm = 0;
+// Clears n 32-bit words (the histograms and counters of a stack).
+__global__ void k_clear(uint32_t *p, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = 0;
+}
+
+int g_pyr_blocks_per_sm[2] = {0, 0};
 
 }  // namespace
 
@@ -218,16 +387,27 @@ cudaError_t launch_pyramid(const uint8_t *images, const mtb_layout_t &L, uint8_t
     const long long per_exp = (long long)tiles_x * tiles_y;
     const long long total = per_exp * L.n;
     if (total > 0x7fffffffLL) return cudaErrorInvalidValue;
-    if (g_pyr_blocks_per_sm == 0) {
-        int nb = 0;
-        cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pyramid, kPyrThreads, 0);
+    const bool aligned = (L.w % 16) == 0;
+    int &nb = g_pyr_blocks_per_sm[aligned ? 1 : 0];
+    if (nb == 0) {
+        int v = 0;
+        cudaError_t err = aligned ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_pyramid<true>, kPyrThreads, 0)
+                                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_pyramid<false>, kPyrThreads, 0);
         if (err != cudaSuccess) return err;
-        g_pyr_blocks_per_sm = nb > 0 ? nb : 1;
+        nb = v > 0 ? v : 1;
     }
-    const long long cap = (long long)device_sm_count() * g_pyr_blocks_per_sm;
+    const long long cap = (long long)device_sm_count() * nb;
     const int grid = (int)(total < cap ? total : cap);
-    k_pyramid<<<grid, kPyrThreads, 0, s>>>(images, L, ws, tiles_x, (int)per_exp, (int)total);
-    return cudaGetLastError();
+    // histograms and counters are adjacent (layout): clear both in one launch
+    const int words = (int)((L.counter_offset + (uint64_t)L.n * sizeof(int32_t) - L.hist_offset) / 4);
+    cudaError_t err = launch_k(k_clear, dim3((words + 1023) / 1024 < 64 ? (words + 1023) / 1024 : 64), dim3(256), s,
+                               false, reinterpret_cast<uint32_t *>(ws + L.hist_offset), words);
+    if (err != cudaSuccess) return err;
+    if (aligned)
+        return launch_k(k_pyramid<true>, dim3(grid), dim3(kPyrThreads), s, true, images, L, ws, tiles_x, (int)per_exp,
+                        (int)total);
+    return launch_k(k_pyramid<false>, dim3(grid), dim3(kPyrThreads), s, true, images, L, ws, tiles_x, (int)per_exp,
+                    (int)total);
 }
 
 }  // namespace mtb

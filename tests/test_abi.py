@@ -102,6 +102,8 @@ def test_layout_invariants(mtb_lib, n, w, h, levels):
     regions.append((lay.median_offset, lay.median_offset + n * levels * 4))
     regions.append((lay.base_offset, lay.base_offset + n * levels * 8))
     regions.append((lay.shift_offset, lay.shift_offset + n * levels * 8))
+    regions.append((lay.counter_offset, lay.counter_offset + (n * (levels + 2) + 16) * 4))
+    regions.append((lay.table_offset, lay.table_offset + n * 1280 * 4))
     regions.append((lay.status_offset, lay.status_offset + 16))
     regions.sort()
     for (a0, a1), (b0, b1) in zip(regions, regions[1:]):

@@ -32,6 +32,11 @@ SHAPES = [
     (3, 1000, 2, 2, 1),
     (777, 555, 9, 5, 3),
     (1024, 1024, 11, 2, 0),
+    # grid-level search launches: 2-D blocks, several word blocks, odd widths
+    (1000, 700, 5, 3, 1),
+    (1001, 333, 4, 2, 1),
+    (4100, 300, 3, 2, 0),
+    (9000, 100, 2, 3, 2),
 ]
 
 
@@ -128,3 +133,23 @@ def test_invalid_arguments_enqueue_nothing(mtb_lib):
     raw = torch.zeros(2 * 8 * 8 * 3 + 1, dtype=torch.uint8, device="cuda")[1:].view(2, 8, 8, 3)
     with pytest.raises(mtb_lib.MtbError):
         mtb_lib.align_stack(raw, 2, 4, 0)  # base not 16-byte aligned
+
+
+def test_bounded_wait_reports_timeout(mtb_lib):
+    """A search whose coarse work for pair 0 never reports completion: the work
+    that depends on it must give up after the timeout and leave MTB_ERR_TIMEOUT
+    in the status word (no hang), and a normal search afterwards is correct."""
+    spec = synth.small_spec(77, 640, 480, n=3, levels=6, shift_range=20, ref=1)
+    imgs = synth.make_stack(spec, "cuda")
+    n, w, h, L = spec.n, spec.w, spec.h, spec.levels
+    ws = mtb_lib.new_workspace(n, w, h, L)
+    mtb_lib.build_pyramids(imgs, L, ws)
+    mtb_lib.build_bitmaps(n, w, h, L, spec.noise_tol, ws)
+    stream = torch.cuda.current_stream().cuda_stream
+    rc = mtb_lib.lib().mtb_debug_search_withheld(n, w, h, L, spec.ref, ws.data_ptr(), ws.numel(), 2_000_000, stream)
+    assert rc == mtb_lib.MTB_ERR_TIMEOUT
+    assert mtb_lib.workspace_status(ws, n, w, h, L) == mtb_lib.MTB_ERR_TIMEOUT
+    shifts = torch.empty((n, 2), dtype=torch.int32, device="cuda")
+    mtb_lib.search_shifts(n, w, h, L, spec.ref, ws, shifts)
+    assert mtb_lib.workspace_status(ws, n, w, h, L) == mtb_lib.MTB_OK
+    assert np.array_equal(shifts.cpu().numpy(), synth.expected_shifts(spec))
