@@ -1,12 +1,14 @@
 #!/usr/bin/env python3
 """Benchmark of the MTB alignment hot path on one or more GB300s.
 
-A step is one pass of the whole path over one exposure stack: the pyramid pass,
-the bitmap pass and the coarse-to-fine shift search, each a C-ABI call
-(mtb_build_pyramids, mtb_build_bitmaps, mtb_search_shifts) on the same stream
-with CUDA events between them.  The default workload is the 4000x3000 stack of
-3 exposures (2 pairs, 7 levels).  The metric is aligned MPix/s: full-resolution
-pixels of every aligned pair divided by the step time.
+A step is one pass of the whole path over one exposure stack: one
+mtb_align_stack_ex call (the pyramid pass, the bitmap pass and the
+coarse-to-fine shift search in one persistent engine launch, after a small
+clearing launch).  The default workload is the 4000x3000 stack of 3 exposures
+(2 pairs, 7 levels).  The metric is aligned MPix/s: full-resolution pixels of
+every aligned pair divided by the step time.  A second loop times the same work
+through the three stage calls (mtb_build_pyramids, mtb_build_bitmaps,
+mtb_search_shifts) with CUDA events between them, for the split by stage.
 
 Inputs and workspaces rotate over several device copies, so between two uses of
 one buffer more than 3x the L2 capacity is written and read: every step starts
@@ -43,12 +45,9 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
-# ncu capture, keyed by kernel and workload, with the SHA-256 of the kernel's
-# source file at capture time; reported only while the source is unchanged.
-NCU_TRAFFIC = {
-    ("pyramid", "stack4000x3000x3"): {"bytes": 118_509_312,
-                                      "source_sha256": "6ab5c5c941879a5e196e704dcc18dd564efc6a4f310e8f94047ae8ce0104aace"},
-}
+# ncu capture, keyed by kernel and workload, with the SHA-256 of the CUDA
+# sources at capture time; reported only while the sources are unchanged.
+NCU_TRAFFIC = {}
 
 
 def parse_args(argv=None):
@@ -123,20 +122,24 @@ def algorithmic_bytes(spec) -> dict:
 
 
 def kernels_per_step(spec) -> int:
-    return 1 + 1 + spec.levels + 1  # pyramid, bitmaps, one shift launch per level, finalize
+    return 2  # k_engine_clear, k_engine
 
 
-def stage_kernel_source(stage: str) -> str:
-    return os.path.join(ROOT, "paper_2007_06483_gb300", "csrc",
-                        {"pyramid": "mtb_pyramid.cu", "bitmaps": "mtb_bitmaps.cu", "search": "mtb_search.cu"}[stage])
+def kernel_sources_digest() -> str:
+    """SHA-256 over the library's CUDA sources (any change voids a stored ncu figure)."""
+    csrc = os.path.join(ROOT, "paper_2007_06483_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()
 
 
-def traffic_for(stage: str, spec):
-    rec = NCU_TRAFFIC.get((stage, spec.name))
+def traffic_for(kernel: str, spec):
+    rec = NCU_TRAFFIC.get((kernel, spec.name))
     if not rec:
         return None
-    digest = hashlib.sha256(open(stage_kernel_source(stage), "rb").read()).hexdigest()
-    return rec["bytes"] if rec["source_sha256"] == digest else None
+    return rec["bytes"] if rec["sources_sha256"] == kernel_sources_digest() else None
 
 
 def hbm_peak():
@@ -252,22 +255,25 @@ def run_gb300(args):
     def step(b, ev=None):
         if ev is not None:
             ev[0].record(stream)
-        mtb.build_pyramids(imgs[b], L, wss[b], stream)
+        mtb.align_stack(imgs[b], L, spec.noise_tol, spec.ref, workspace=wss[b], out=shifts[b], stream=stream)
         if ev is not None:
             ev[1].record(stream)
+
+    def staged(b, ev):
+        ev[0].record(stream)
+        mtb.build_pyramids(imgs[b], L, wss[b], stream)
+        ev[1].record(stream)
         mtb.build_bitmaps(n, w, h, L, spec.noise_tol, wss[b], stream)
-        if ev is not None:
-            ev[2].record(stream)
+        ev[2].record(stream)
         mtb.search_shifts(n, w, h, L, spec.ref, wss[b], shifts[b], None, None, stream)
-        if ev is not None:
-            ev[3].record(stream)
+        ev[3].record(stream)
 
     for k in range(max(3, args.warmup)):
         step(k % B)
     torch.cuda.synchronize(dev)
 
     K = args.steps
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(K)]
     sampler = ClockSampler(dev.index if dev.index is not None else 0)
     sampler.start()
     barrier(world)
@@ -280,15 +286,23 @@ def run_gb300(args):
     barrier(world)
     clocks = sampler.stop()
 
-    total_ms = evs[0][0].elapsed_time(evs[-1][3])
-    step_ms = [e[0].elapsed_time(e[3]) for e in evs]
-    stage_ms = {
-        "pyramid": statistics.mean(e[0].elapsed_time(e[1]) for e in evs),
-        "bitmaps": statistics.mean(e[1].elapsed_time(e[2]) for e in evs),
-        "search": statistics.mean(e[2].elapsed_time(e[3]) for e in evs),
-    }
+    total_ms = evs[0][0].elapsed_time(evs[-1][1])
+    step_ms = [e[0].elapsed_time(e[1]) for e in evs]
     total_ms = max_over_ranks(total_ms, world, dev)
     ms_per_step = total_ms / K
+
+    # the same work through the three stage calls, for the split by stage
+    sev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(max(3, min(K, 20)))]
+    for k in range(3):
+        staged(k % B, sev[k])
+    for k, ev in enumerate(sev):
+        staged(k % B, ev)
+    torch.cuda.synchronize(dev)
+    stage_ms = {
+        "pyramid": statistics.mean(e[0].elapsed_time(e[1]) for e in sev),
+        "bitmaps": statistics.mean(e[1].elapsed_time(e[2]) for e in sev),
+        "search": statistics.mean(e[2].elapsed_time(e[3]) for e in sev),
+    }
     value = world * spec.aligned_pixels / (ms_per_step / 1e3) / 1e6
 
     # correctness of what was timed: every buffer's shifts vs the planted ones
@@ -297,16 +311,16 @@ def run_gb300(args):
 
     abytes = algorithmic_bytes(spec)
     peak, peak_kind = hbm_peak()
-    dom = max(stage_ms, key=stage_ms.get)
-    achieved = abytes[dom] / (stage_ms[dom] / 1e3) / 1e9
-    roofline = {"bound": "hbm", "kernel": {"pyramid": "k_pyramid", "bitmaps": "k_bitmaps",
-                                           "search": "k_shift x levels + k_finalize"}[dom],
+    step_bytes = sum(abytes.values())
+    # the engine launch is the step's one big kernel; its duration is the step
+    # (plus the clearing launch of a few microseconds)
+    achieved = step_bytes / (ms_per_step / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "k_engine (after k_engine_clear)",
                 "achieved": round(achieved, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": traffic_for(dom, spec),
-                "algorithmic_bytes_per_launch": abytes[dom]}
+                "frac": round(achieved / peak, 4), "traffic": traffic_for("engine", spec),
+                "algorithmic_bytes_per_launch": step_bytes}
     stages = {k: {"ms": round(v, 5), "alg_GBps": round(abytes[k] / (v / 1e3) / 1e9, 1),
                   "frac_of_peak": round(abytes[k] / (v / 1e3) / 1e9 / peak, 4)} for k, v in stage_ms.items()}
-    step_bytes = sum(abytes.values())
 
     # ---- end to end through the host-buffer entry point ----
     e2e = None
@@ -413,10 +427,100 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------- batched form
+def run_batch(args):
+    """Uneven stacks (synth.batch_specs) in one persistent graph-captured launch,
+    after the autotuner picked its tile shapes; the same stacks through the
+    plain per-stack path for comparison.  A step aligns every stack once."""
+    import numpy as np
+    import torch
+
+    from paper_2007_06483_gb300 import build as cuda_build
+
+    cuda_build.build()
+    import paper_2007_06483_gb300 as mtb
+    from paper_2007_06483_gb300 import synth
+
+    count = int(args.workload[len("batch"):] or 256)
+    specs = synth.batch_specs(count)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stacks = [{"images": synth.make_stack(sp, dev), "levels": sp.levels, "noise_tol": sp.noise_tol,
+               "ref_idx": sp.ref} for sp in specs]
+    pixels = sum(sp.aligned_pixels for sp in specs)
+    abytes = sum(sum(algorithmic_bytes(sp).values()) for sp in specs)
+    stream = torch.cuda.current_stream(dev)
+    batch = mtb.Batch(stacks, level_outputs=False)
+    batch.tune(reps=2, stream=stream)
+    cfg = batch.config()
+    for _ in range(max(3, args.warmup)):
+        batch.run(stream)
+    torch.cuda.synchronize(dev)
+    K = args.steps
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(K)]
+    sampler = ClockSampler(dev.index or 0)
+    sampler.start()
+    for k in range(K):
+        evs[k][0].record(stream)
+        batch.run(stream)
+        evs[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    assert batch.status() == mtb.MTB_OK
+    step_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    ms = evs[0][0].elapsed_time(evs[-1][1]) / K
+    expected_ok = sum(np.array_equal(batch.shifts[k].cpu().numpy(), synth.expected_shifts(sp))
+                      for k, sp in enumerate(specs))
+
+    # the same stacks through the plain path, one stack after the other
+    wss = [mtb.new_workspace(sp.n, sp.w, sp.h, sp.levels, device=dev) for sp in specs]
+    outs = [torch.empty((sp.n, 2), dtype=torch.int32, device=dev) for sp in specs]
+
+    def plain():
+        for k, st in enumerate(stacks):
+            mtb.align_stack(st["images"], st["levels"], st["noise_tol"], st["ref_idx"], workspace=wss[k],
+                            out=outs[k], stream=stream)
+
+    plain()
+    torch.cuda.synchronize(dev)
+    same = all(torch.equal(outs[k], batch.shifts[k]) for k in range(count))
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    Kp = max(1, min(K, 5))
+    p0.record(stream)
+    for _ in range(Kp):
+        plain()
+    p1.record(stream)
+    torch.cuda.synchronize(dev)
+    plain_ms = p0.elapsed_time(p1) / Kp
+    peak, peak_kind = hbm_peak()
+    achieved = abytes / (ms / 1e3) / 1e9
+    line = {
+        "metric": METRIC + " (batched)", "value": round(pixels / (ms / 1e3) / 1e6, 2), "unit": UNIT, "n_gpus": 1,
+        "steps": K, "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": f"batch{count}", "stacks": count, "exposures": sum(sp.n for sp in specs),
+                   "pairs": sum(sp.pairs for sp in specs), "aligned_mpix": round(pixels / 1e6, 1),
+                   "tile_shapes": cfg, "l2": "inputs of the batch far exceed L2"},
+        "plain_path": {"value": round(pixels / (plain_ms / 1e3) / 1e6, 2), "ms_per_step": round(plain_ms, 4),
+                       "same_shifts_as_batch": bool(same)},
+        "batch_vs_plain": round(plain_ms / ms, 3),
+        "latency_ms": {"p50": round(statistics.median(step_ms), 4), "p99": round(max(step_ms), 4)},
+        "hbm_gbs": round(achieved, 1),
+        "roofline": {"bound": "hbm", "kernel": "k_engine<batch> (after k_engine_clear)", "achieved": round(achieved, 1),
+                     "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "traffic": None, "algorithmic_bytes_per_launch": abytes},
+        "gpu_launches": 2 * K, "clocks": clocks,
+        "planted_shifts_recovered": f"{expected_ok}/{count} stacks",
+    }
+    print(json.dumps(line), flush=True)
+    batch.close()
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload.startswith("batch"):
+        run_batch(args)
     else:
         run_gb300(args)
 

@@ -76,7 +76,7 @@ extern "C" {
  *   shift        int32  [n][levels][2]   (best shift chosen at each level)
  *   table        uint32 [n][1280]         (candidate errors of whole search windows
  *                                         at the coarsest levels, per pair)
- *   counters     int32  [n * (levels + 2) + 16] (completion counters of the kernels)
+ *   counters     int32  [n * (2 * levels + 4) + 16] (completion counters of the kernels)
  *   status       int32 [4]               (device status words) */
 typedef struct mtb_layout {
     int32_t n, w, h, levels;
@@ -182,6 +182,57 @@ size_t mtb_host_workspace_bytes(int n_exposures, int w, int h, int levels);
 int mtb_align_stack_host(const uint8_t *host_images, int n_exposures, int w, int h, int levels,
                          int noise_tol, int ref_idx, int32_t *host_shifts_out,
                          void *device_workspace, size_t device_workspace_bytes, void *stream);
+
+/* ---- Batches: many stacks of any sizes in one persistent launch ----------
+ * Sec. III-B aligns one stack's pairs with each exposure's pyramid built once;
+ * a batch does that for many stacks together.  Every step of every stack runs
+ * as work items of one persistent kernel (after one small clearing kernel),
+ * queued in topological order with per-item completion counters, so the
+ * latency-bound coarse-to-fine searches of some stacks overlap the
+ * bandwidth-bound pyramid and bitmap work of others.  Results are exactly those
+ * of mtb_align_stack_ex for each stack. */
+typedef struct mtb_stack_desc {
+    const uint8_t *images;      /* device [n][h][w][3] uint8, 16-byte aligned */
+    int n_exposures, w, h, levels, noise_tol, ref_idx;  /* as for mtb_align_stack */
+    int32_t *shifts_out;        /* device int32 [n][2] */
+    uint32_t *level_errs_out;   /* device uint32 [n][levels][9] or NULL */
+    int32_t *level_shifts_out;  /* device int32 [n][levels][2] or NULL */
+} mtb_stack_desc_t;
+
+typedef struct mtb_batch mtb_batch_t;
+
+/* Device workspace a batch of these stacks needs (0 if a stack is invalid). */
+size_t mtb_batch_workspace_bytes(const mtb_stack_desc_t *stacks, int count);
+
+/* Plans a batch: checks every stack (MTB_ERR_INVALID_ARG on the first invalid
+ * one), lays the stacks out in `workspace` (device, 256-byte aligned, >=
+ * mtb_batch_workspace_bytes; NULL to let the batch cudaMalloc its own), uploads
+ * the work tables and captures the launch in a CUDA graph.  Synchronous; the
+ * descriptors are copied, the buffers they point to must stay valid while the
+ * batch is used.  *out receives the batch. */
+int mtb_batch_create(const mtb_stack_desc_t *stacks, int count, void *workspace, size_t workspace_bytes,
+                     mtb_batch_t **out);
+
+/* Enqueues one run of the batch on `stream` (aligns every stack from the
+ * current contents of its image buffer). */
+int mtb_batch_run(mtb_batch_t *batch, void *stream);
+
+/* Autotuner: times `reps` runs of the batch for each candidate tile shape (runs
+ * of pyramid tiles per CTA, words per bitmap chunk, search chunks per level),
+ * coordinate by coordinate, and keeps the fastest.  Synchronous. */
+int mtb_batch_tune(mtb_batch_t *batch, int reps, void *stream);
+
+/* The batch's tile shapes: values[0] pyramid runs per CTA, values[1] words per
+ * bitmap chunk, values[2] search chunks per level (x CTAs / stacks), values[3]
+ * 1 if the launch is a CUDA graph.  n_values >= 4. */
+int mtb_batch_config(const mtb_batch_t *batch, int *values, int n_values);
+
+/* Waits for `stream`, then returns MTB_OK or the first stack's non-zero status
+ * word (MTB_ERR_TIMEOUT if a bounded device wait gave up). */
+int mtb_batch_status(mtb_batch_t *batch, void *stream);
+
+/* Frees the batch (and its workspace if it allocated it).  NULL is ignored. */
+void mtb_batch_destroy(mtb_batch_t *batch);
 
 /* Size of the fixed device scratch array used by mtb_align_stack_noalloc:
  * 32 MiB, enough for a stack of five 3.7 MP exposures at 6 levels. */

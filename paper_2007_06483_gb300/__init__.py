@@ -60,6 +60,17 @@ class Layout(ctypes.Structure):
     ]
 
 
+class StackDesc(ctypes.Structure):
+    """Mirror of mtb_stack_desc_t."""
+
+    _fields_ = [
+        ("images", ctypes.c_void_p),
+        ("n_exposures", ctypes.c_int), ("w", ctypes.c_int), ("h", ctypes.c_int), ("levels", ctypes.c_int),
+        ("noise_tol", ctypes.c_int), ("ref_idx", ctypes.c_int),
+        ("shifts_out", ctypes.c_void_p), ("level_errs_out", ctypes.c_void_p), ("level_shifts_out", ctypes.c_void_p),
+    ]
+
+
 def library_path() -> str:
     return LIB_PATH
 
@@ -88,6 +99,13 @@ def lib():
             "mtb_align_stack_host": (I, [P, I, I, I, I, I, I, P, P, S, P]),
             "mtb_workspace_status": (I, [P, S, I, I, I, I, P]),
             "mtb_debug_search_withheld": (I, [I, I, I, I, I, P, S, ctypes.c_longlong, P]),
+            "mtb_batch_workspace_bytes": (S, [P, I]),
+            "mtb_batch_create": (I, [P, I, P, S, ctypes.POINTER(ctypes.c_void_p)]),
+            "mtb_batch_run": (I, [P, P]),
+            "mtb_batch_tune": (I, [P, I, P]),
+            "mtb_batch_config": (I, [P, ctypes.POINTER(ctypes.c_int), I]),
+            "mtb_batch_status": (I, [P, P]),
+            "mtb_batch_destroy": (None, [P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -155,15 +173,15 @@ def new_workspace(n: int, w: int, h: int, levels: int, device="cuda"):
 
 
 def align_stack(images, levels: int, noise_tol: int = 4, ref_idx: int = 0, *, level_outputs: bool = False,
-                workspace=None, stream=None):
+                workspace=None, out=None, stream=None):
     """Align a [n, h, w, 3] uint8 CUDA stack; returns int32 [n, 2] shifts on the
     device (and, with level_outputs, uint32 [n, levels, 9] errors and int32
-    [n, levels, 2] per-level shifts)."""
+    [n, levels, 2] per-level shifts).  `out` may hold the int32 [n, 2] result."""
     import torch
 
     n, w, h = _dims(images)
     dev = images.device
-    shifts = torch.empty((n, 2), dtype=torch.int32, device=dev)
+    shifts = out if out is not None else torch.empty((n, 2), dtype=torch.int32, device=dev)
     errs = lsh = None
     if level_outputs:
         errs = torch.empty((n, levels, 9), dtype=torch.int32, device=dev)  # viewed as uint32
@@ -287,3 +305,76 @@ def align_stack_noalloc(images, levels: int, noise_tol: int = 4, ref_idx: int = 
     _check(_noalloc_fn(images.data_ptr(), n, w, h, levels, noise_tol, ref_idx, shifts.data_ptr(), errs.data_ptr(),
                        lsh.data_ptr(), _stream(stream)), "mtb_align_stack_noalloc")
     return shifts, errs, lsh
+
+
+class Batch:
+    """Many stacks aligned in one persistent launch (mtb_batch_* of the C ABI).
+
+    stacks: list of dicts with keys images (uint8 CUDA tensor [n, h, w, 3]),
+    levels, noise_tol, ref_idx.  Output tensors are allocated here: after run(),
+    shifts[i] ([n, 2] int32), level_errs[i] ([n, levels, 9], uint32 viewed as
+    int32) and level_shifts[i] ([n, levels, 2]) hold stack i's results."""
+
+    def __init__(self, stacks, level_outputs: bool = True, workspace=None):
+        import torch
+
+        self._keep = []
+        descs = (StackDesc * len(stacks))()
+        self.shifts, self.level_errs, self.level_shifts = [], [], []
+        for k, st in enumerate(stacks):
+            imgs = st["images"]
+            n, w, h = _dims(imgs)
+            L = int(st["levels"])
+            dev = imgs.device
+            sh = torch.zeros((n, 2), dtype=torch.int32, device=dev)
+            er = torch.zeros((n, L, 9), dtype=torch.int32, device=dev) if level_outputs else None
+            ls = torch.zeros((n, L, 2), dtype=torch.int32, device=dev) if level_outputs else None
+            self.shifts.append(sh)
+            self.level_errs.append(er)
+            self.level_shifts.append(ls)
+            self._keep.append(imgs)
+            descs[k] = StackDesc(imgs.data_ptr(), n, w, h, L, int(st.get("noise_tol", 4)), int(st.get("ref_idx", 0)),
+                                 sh.data_ptr(), _ptr(er), _ptr(ls))
+        self._descs = descs
+        handle = ctypes.c_void_p()
+        ws_ptr, ws_bytes = None, 0
+        if workspace is not None:
+            ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel()
+            self._keep.append(workspace)
+        _check(lib().mtb_batch_create(ctypes.cast(descs, ctypes.c_void_p), len(stacks), ws_ptr, ws_bytes,
+                                      ctypes.byref(handle)), "mtb_batch_create")
+        self._h = handle
+
+    @staticmethod
+    def workspace_bytes(stacks) -> int:
+        descs = (StackDesc * len(stacks))()
+        for k, st in enumerate(stacks):
+            n, w, h = _dims(st["images"])
+            descs[k] = StackDesc(st["images"].data_ptr(), n, w, h, int(st["levels"]), int(st.get("noise_tol", 4)),
+                                 int(st.get("ref_idx", 0)), 1 << 20, None, None)
+        return int(lib().mtb_batch_workspace_bytes(ctypes.cast(descs, ctypes.c_void_p), len(stacks)))
+
+    def run(self, stream=None):
+        _check(lib().mtb_batch_run(self._h, _stream(stream)), "mtb_batch_run")
+
+    def tune(self, reps: int = 3, stream=None):
+        _check(lib().mtb_batch_tune(self._h, reps, _stream(stream)), "mtb_batch_tune")
+
+    def config(self) -> dict:
+        v = (ctypes.c_int * 4)()
+        _check(lib().mtb_batch_config(self._h, v, 4), "mtb_batch_config")
+        return {"pyr_runs_per_cta": v[0], "bit_chunk_words": v[1], "search_waves": v[2], "graph": bool(v[3])}
+
+    def status(self, stream=None) -> int:
+        return int(lib().mtb_batch_status(self._h, _stream(stream)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().mtb_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -69,7 +69,7 @@ int compute_layout(int n, int w, int h, int levels, mtb_layout_t *L) {
     L->hist_offset = off;
     off += (size_t)n * levels * 256 * sizeof(uint32_t);
     L->counter_offset = off;  // right after hist: the pyramid stage clears both in one launch
-    off += (size_t)(n * (levels + 2) + 16) * sizeof(int32_t);
+    off += (size_t)(n * (2 * levels + 4) + 16) * sizeof(int32_t);
     off = align_up(off, 256);
     L->errs_offset = off;
     off += (size_t)n * levels * 9 * sizeof(uint32_t);
@@ -96,6 +96,9 @@ int stage_pyramid(const uint8_t *images, const mtb_layout_t &L, uint8_t *ws, cud
     return cuda_status(launch_pyramid(images, L, ws, s));
 }
 
+// One stack: the three stage kernels chained with programmatic dependent launch
+// (lower latency for a single stack than the engine, whose strength is
+// overlapping many stacks in a batch).
 int run_all(const uint8_t *images, const mtb_layout_t &L, int tol, int ref, uint8_t *ws, int32_t *shifts_out,
             uint32_t *level_errs_out, int32_t *level_shifts_out, cudaStream_t s) {
     int rc = stage_pyramid(images, L, ws, s);

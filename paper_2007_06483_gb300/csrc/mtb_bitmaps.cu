@@ -19,113 +19,10 @@
 // bytes because each byte of the minuend is >= 0x80).  The 4 MSBs of a word are
 // gathered into 4 adjacent bits by one multiply: bits 7, 15, 23, 31 times
 // 2^21 + 2^14 + 2^7 + 1 land on bits 28..31 without carries.
-#include "mtb_device.cuh"
+#include "mtb_bitmaps_dev.cuh"
 
 namespace mtb {
 namespace {
-
-constexpr uint32_t kHi = 0x80808080u;
-constexpr uint32_t kLo7 = 0x7f7f7f7fu;
-
-// Per-byte x >= t test for a fixed t in [0, 255], result in each byte's MSB.
-struct ByteGE {
-    uint32_t t_lo7, not_t;
-    __device__ __forceinline__ explicit ByteGE(uint32_t t) {
-        const uint32_t T = t * 0x01010101u;
-        t_lo7 = T & kLo7;
-        not_t = ~T;
-    }
-    __device__ __forceinline__ uint32_t operator()(uint32_t x) const {
-        const uint32_t d = (x | kHi) - t_lo7;
-        return (x & not_t) | ((x ^ not_t) & d);
-    }
-};
-
-// The thresholds of one (exposure, level): tb = [g >= m + 1], eb = [g < lo] or
-// [g >= hi + 1]; a test that can never hold is masked out instead.
-struct Thresholds {
-    ByteGE tb, lo, hi;
-    uint32_t tb_mask, hi_mask;
-    __device__ __forceinline__ Thresholds(int m, int tol)
-        : tb((uint32_t)min(m + 1, 255)), lo((uint32_t)max(m - tol, 0)), hi((uint32_t)min(m + tol + 1, 255)),
-          tb_mask(m < 255 ? kHi : 0u), hi_mask(m + tol < 255 ? kHi : 0u) {}
-};
-
-// MSBs of bytes 0..3 of x (already masked to kHi) -> bits 0..3.
-__device__ __forceinline__ uint32_t msb_nibble_top(uint32_t x) { return x * 0x00204081u; }
-
-// tb and eb words of 32 gray pixels in 8 little-endian words; only the first
-// nvalid pixels can be set.
-__device__ __forceinline__ uint2 pack_bits(const uint32_t (&v)[8], const Thresholds &th, int nvalid) {
-    uint32_t tb = 0, eb = 0;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        const uint32_t tm = th.tb(v[k]) & th.tb_mask;
-        const uint32_t em = (~th.lo(v[k]) | (th.hi(v[k]) & th.hi_mask)) & kHi;
-        // top nibble of the product holds the 4 flags; move it to bits 4k..4k+3
-        const uint32_t pt = msb_nibble_top(tm), pe = msb_nibble_top(em);
-        if (k == 7) {
-            tb |= pt & 0xf0000000u;
-            eb |= pe & 0xf0000000u;
-        } else {
-            tb |= (pt >> (28 - 4 * k)) & (0xfu << (4 * k));
-            eb |= (pe >> (28 - 4 * k)) & (0xfu << (4 * k));
-        }
-    }
-    const uint32_t keep = nvalid >= 32 ? 0xffffffffu : ((1u << nvalid) - 1u);
-    return make_uint2(tb & keep, eb & keep);
-}
-
-// Levels tile_levels..levels-1 of exposure e, built by one CTA.  Each level
-// reads the previous one, which this CTA wrote itself for all but the first,
-// so those reads go through L2 (ld.global.cg) after a CTA barrier.
-__device__ void deep_levels(const mtb_layout_t &L, uint8_t *ws, int tol, int e, uint32_t *s_hist, int *s_med) {
-    const int tid = threadIdx.x;
-    for (int l = L.tile_levels; l < L.levels; ++l) {
-        for (int v = tid; v < 256; v += blockDim.x) s_hist[v] = 0;
-        __syncthreads();
-        const uint8_t *src = Planes::gray(ws, L, e, l - 1);
-        const int spitch = L.gray_pitch[l - 1];
-        uint8_t *dst = Planes::gray(ws, L, e, l);
-        const int Wl = L.width[l], Hl = L.height[l], gpl = L.gray_pitch[l];
-        const int npx = Wl * Hl;
-        for (int idx = tid; idx < npx; idx += blockDim.x) {
-            const int y = idx / Wl, x = idx - y * Wl;
-            const uint8_t *s0 = src + (size_t)(2 * y) * spitch + 2 * x;
-            const uint8_t *s1 = s0 + spitch;
-            const uint32_t v = box2(__ldcg(s0), __ldcg(s0 + 1), __ldcg(s1), __ldcg(s1 + 1));
-            dst[(size_t)y * gpl + x] = (uint8_t)v;
-            atomicAdd(s_hist + v, 1u);
-        }
-        __syncthreads();
-        uint32_t *gh = Planes::hist(ws, L, e, l);
-        for (int v = tid; v < 256; v += blockDim.x) gh[v] = s_hist[v];
-        if (tid < 32) {
-            const int m = warp_median<false>(s_hist);
-            if (tid == 0) {
-                *s_med = m;
-                *Planes::median(ws, L, e, l) = m;
-            }
-        }
-        __syncthreads();
-        const Thresholds th(*s_med, tol);
-        const int bp = L.bits_pitch[l];
-        uint2 *out = Planes::bits(ws, L, e, l);
-        for (int idx = tid; idx < bp * Hl; idx += blockDim.x) {
-            const int y = idx / bp, q = idx - y * bp;
-            const int x = q * 32;
-            uint2 r = make_uint2(0u, 0u);
-            if (x < Wl) {
-                const uint4 *p = reinterpret_cast<const uint4 *>(dst + (size_t)y * gpl + x);
-                const uint4 a = __ldcg(p), b = __ldcg(p + 1);
-                const uint32_t v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-                r = pack_bits(v, th, min(32, Wl - x));
-            }
-            out[idx] = r;
-        }
-        __syncthreads();
-    }
-}
 
 __global__ void __launch_bounds__(kBitThreads)
 k_bitmaps(const mtb_layout_t L, uint8_t *__restrict__ ws, int tol, int deep_ctas, int chunks_per_exp) {
@@ -139,35 +36,9 @@ k_bitmaps(const mtb_layout_t L, uint8_t *__restrict__ ws, int tol, int deep_ctas
     }
     const int item = blockIdx.x - deep_ctas;
     const int e = item / chunks_per_exp;
-    int c = item - e * chunks_per_exp;
-    int l = 0;
-    for (; l < L.tile_levels - 1; ++l) {
-        const int words = L.bits_pitch[l] * L.height[l];
-        const int ch = (words + kBitWordsPerCta - 1) / kBitWordsPerCta;
-        if (c < ch) break;
-        c -= ch;
-    }
-    if (threadIdx.x == 0) s_med = *Planes::median(ws, L, e, l);
-    __syncthreads();
-    const Thresholds th(s_med, tol);
-    const int Wl = L.width[l], Hl = L.height[l], bp = L.bits_pitch[l], gpl = L.gray_pitch[l];
-    const uint8_t *g = Planes::gray(ws, L, e, l);
-    uint2 *out = Planes::bits(ws, L, e, l);
-    const int words = bp * Hl;
-    const int w_end = min(words, (c + 1) * kBitWordsPerCta);
-#pragma unroll 4
-    for (int idx = c * kBitWordsPerCta + threadIdx.x; idx < w_end; idx += kBitThreads) {
-        const int y = idx / bp, q = idx - y * bp;
-        const int x = q * 32;
-        uint2 r = make_uint2(0u, 0u);
-        if (x < Wl) {
-            const uint4 *p = reinterpret_cast<const uint4 *>(g + (size_t)y * gpl + x);
-            const uint4 a = __ldcs(p), b = __ldcs(p + 1);
-            const uint32_t v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-            r = pack_bits(v, th, min(32, Wl - x));
-        }
-        out[idx] = r;
-    }
+    int l, c;
+    bitmap_chunk_of(L, item - e * chunks_per_exp, kBitWordsPerCta, &l, &c);
+    bitmap_chunk(L, ws, tol, e, l, c, kBitWordsPerCta, &s_med);
 }
 
 }  // namespace

@@ -55,15 +55,72 @@ __device__ __forceinline__ int warp_median(const uint32_t *hist) {
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
-__device__ __forceinline__ int32_t *counters(uint8_t *ws, const mtb_layout_t &L) {
+__host__ __device__ __forceinline__ int32_t *counters(uint8_t *ws, const mtb_layout_t &L) {
     return reinterpret_cast<int32_t *>(ws + L.counter_offset);
 }
 
-// Counter area: [0, n) pyramid tiles finished per exposure; n + kCtrQueue the
-// search's work-queue head; from n + kCtrDone, done[pair][level] (chunks of a
-// level of a pair finished), then brute[pair] (window rows of a pair's coarse
-// levels finished).
-enum CounterSlot { kCtrQueue = 0, kCtrDone = 8 };
+// The counter area of a stack (int32, layout counter_offset):
+//   tiles[e]          pyramid tiles of exposure e finished
+//   pyr_ready[e]      1 once exposure e's pyramid, histograms and medians are done
+//   bit_done[e][l]    bitmap chunks of exposure e, level l finished
+//   queue             work-queue head of a search or engine launch
+//   done[p][l]        search chunks of pair p, level l finished
+//   window[p]         window items of pair p finished
+// The pyramid stage clears everything up to bit_done; the search stage the rest.
+struct Ctr {
+    static __device__ __forceinline__ int32_t *tiles(uint8_t *ws, const mtb_layout_t &L, int e) {
+        return counters(ws, L) + e;
+    }
+    static __device__ __forceinline__ int32_t *pyr_ready(uint8_t *ws, const mtb_layout_t &L, int e) {
+        return counters(ws, L) + L.n + e;
+    }
+    static __device__ __forceinline__ int32_t *bit_done(uint8_t *ws, const mtb_layout_t &L, int e, int l) {
+        return counters(ws, L) + 2 * L.n + e * L.levels + l;
+    }
+    static __device__ __forceinline__ int32_t *queue(uint8_t *ws, const mtb_layout_t &L) {
+        return counters(ws, L) + 2 * L.n + L.n * L.levels;
+    }
+    static __host__ __forceinline__ int32_t *queue_host(uint8_t *ws, const mtb_layout_t &L) {
+        return counters(ws, L) + 2 * L.n + L.n * L.levels;
+    }
+    static __device__ __forceinline__ int32_t *done(uint8_t *ws, const mtb_layout_t &L, int p, int l) {
+        return counters(ws, L) + 2 * L.n + L.n * L.levels + 8 + p * L.levels + l;
+    }
+    static __device__ __forceinline__ int32_t *window(uint8_t *ws, const mtb_layout_t &L, int p) {
+        return counters(ws, L) + 2 * L.n + 2 * L.n * L.levels + 8 + p;
+    }
+};
+// int32 words of the counter area cleared by the pyramid and by the search stage
+// (together 3n + 2 n levels + 8, within the n (2 levels + 4) + 16 of the layout)
+__host__ __device__ __forceinline__ int pyramid_counter_words(const mtb_layout_t &L) { return 2 * L.n + L.n * L.levels; }
+__host__ __device__ __forceinline__ int search_counter_words(const mtb_layout_t &L) { return 8 + L.n * L.levels + L.n; }
+
+// Bitmap chunks of tile level l of one exposure, and the value of bit_done[e][l]
+// once level l of an exposure is complete (deep levels are built whole).
+// (chunk_words: words per bitmap chunk, kBitWordsPerCta for the stage kernel)
+__host__ __device__ __forceinline__ int bitmap_chunks(const mtb_layout_t &L, int l, int chunk_words) {
+    return (L.bits_pitch[l] * L.height[l] + chunk_words - 1) / chunk_words;
+}
+__host__ __device__ __forceinline__ int bitmap_target(const mtb_layout_t &L, int l, int chunk_words) {
+    return l < L.tile_levels ? bitmap_chunks(L, l, chunk_words) : 1;
+}
+
+// Adds 1 to a completion counter after this CTA's writes: every thread fences
+// its own writes, the CTA synchronises, then one thread adds.
+__device__ __forceinline__ void cta_signal(int32_t *ctr, int add = 1) {
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) atomicAdd(ctr, add);
+}
+
+// Weak global load that may be served from L1.  Unlike ld.global.nc it stays
+// correct for data another CTA of the same launch wrote before a completion
+// counter that this CTA acquired.
+__device__ __forceinline__ uint2 ld_weak(const uint2 *p) {
+    uint2 v;
+    asm volatile("ld.global.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
+    return v;
+}
 
 __device__ __forceinline__ int32_t *status_word(uint8_t *ws, const mtb_layout_t &L) {
     return reinterpret_cast<int32_t *>(ws + L.status_offset);

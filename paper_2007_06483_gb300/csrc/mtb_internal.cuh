@@ -112,6 +112,11 @@ cudaError_t launch_search_ex(const mtb_layout_t &L, int ref_idx, uint8_t *ws, in
 
 int device_sm_count();
 
+// Whole alignment of one stack in one persistent launch (mtb_engine.cu).
+cudaError_t launch_engine_single(const mtb_layout_t &L, const uint8_t *images, uint8_t *ws, int tol, int ref,
+                                 int32_t *shifts_out, uint32_t *level_errs_out, int32_t *level_shifts_out,
+                                 cudaStream_t s);
+
 // Launches kernel<<<grid, block, 0, s>>>(args...).  With `after_previous` the
 // launch carries the programmatic-stream-serialization attribute: it may begin
 // while the previous kernel in the stream runs, and the kernel orders its

@@ -1,0 +1,309 @@
+// mtb_pyramid_dev.cuh -- device functions of the pyramid pass (gray, levels
+// 1..5 of a tile, histograms, medians), shared by the stage kernel and the
+// engine.
+#pragma once
+
+#include "mtb_device.cuh"
+
+namespace mtb {
+namespace {
+
+// Offset of level l's tile inside the shared level buffer.
+__host__ __device__ constexpr int lv_offset(int l) {
+    int off = 0;
+    for (int k = 0; k < l; ++k) off += (kTileRows >> k) * (kTileCols >> k);
+    return off;
+}
+constexpr int kLvBytes = lv_offset(kTileLog2 + 1);
+
+struct PyrShared {
+    alignas(16) uint8_t lv[kLvBytes];
+    uint32_t h01[2][kPyrWarps][256];  // warp-private, levels 0 and 1
+    uint32_t hs[kTileLog2 - 1][256];  // levels 2..5, one per CTA
+    int last;
+};
+
+// Q14 luma weights split into high and low bytes: w = 256 * hi + lo, so two
+// byte dot products give the weighted sum exactly.
+constexpr uint32_t kWHi = 19u | (37u << 8) | (7u << 16);
+constexpr uint32_t kWLo = 35u | (145u << 8) | (76u << 16);
+static_assert(19 * 256 + 35 == 4899 && 37 * 256 + 145 == 9617 && 7 * 256 + 76 == 1868, "Q14 weight split");
+
+// Gray of the pixel whose R, G, B are bytes 0..2 (lo3) or 1..3 (hi3) of a word.
+__device__ __forceinline__ uint32_t luma_lo3(uint32_t w) {
+    return (__dp4a(w, kWHi, 0u) * 256u + __dp4a(w, kWLo, 8192u)) >> 14;
+}
+__device__ __forceinline__ uint32_t luma_hi3(uint32_t w) {
+    return (__dp4a(w, kWHi << 8, 0u) * 256u + __dp4a(w, kWLo << 8, 8192u)) >> 14;
+}
+
+// 4 pixels = 12 RGB bytes in words w0..w2 -> their gray values and the packed word.
+__device__ __forceinline__ uint32_t gray4(uint32_t w0, uint32_t w1, uint32_t w2, uint32_t *g) {
+    g[0] = luma_lo3(w0);
+    g[1] = luma_lo3(__byte_perm(w0, w1, 0x0543));  // bytes 3, 4, 5
+    g[2] = luma_lo3(__byte_perm(w1, w2, 0x0432));  // bytes 6, 7, 8
+    g[3] = luma_hi3(w2);                          // bytes 9, 10, 11
+    return __byte_perm(__byte_perm(g[0], g[1], 0x3340), __byte_perm(g[2], g[3], 0x3340), 0x5410);
+}
+
+// 16 pixels of one 48-byte group -> gray values and 4 packed words.
+__device__ __forceinline__ uint4 gray16(const uint4 &a, const uint4 &b, const uint4 &c, uint32_t (&g)[16]) {
+    uint4 v;
+    v.x = gray4(a.x, a.y, a.z, g + 0);
+    v.y = gray4(a.w, b.x, b.y, g + 4);
+    v.z = gray4(b.z, b.w, c.x, g + 8);
+    v.w = gray4(c.y, c.z, c.w, g + 12);
+    return v;
+}
+
+// Histogram of a group's pixels q in [qa, qb); one atomic if all 16 are equal.
+__device__ __forceinline__ void hist_group(uint32_t *h, const uint32_t (&g)[16], const uint4 &v, int qa, int qb) {
+    const uint32_t b0 = __byte_perm(v.x, 0u, 0x0000u);
+    if (qa == 0 && qb == 16 && v.x == b0 && v.y == b0 && v.z == b0 && v.w == b0) {
+        atomicAdd(h + g[0], 16u);
+        return;
+    }
+#pragma unroll
+    for (int q = 0; q < 16; ++q)
+        if (q >= qa && q < qb) atomicAdd(h + g[q], 1u);
+}
+
+// Two shrunk pixels (16-bit lanes) from 4 pixels of each of two rows.
+__device__ __forceinline__ uint32_t shrink2(uint32_t a, uint32_t b) {
+    const uint32_t s = __byte_perm(a, 0u, 0x4240u) + __byte_perm(a, 0u, 0x4341u) + __byte_perm(b, 0u, 0x4240u) +
+                       __byte_perm(b, 0u, 0x4341u) + 0x00020002u;
+    return (s >> 2) & 0x00ff00ffu;
+}
+
+// ---- level 0 of one tile: gray into shared memory (and global), histogram ----
+// W is a multiple of 16: every tile row is a whole number of aligned groups.
+__device__ __forceinline__ void tile_level0_aligned(const uint8_t *__restrict__ images, const mtb_layout_t &L,
+                                                    uint8_t *ws, int e, int y0, int x0, int rows, int cols,
+                                                    PyrShared &sm) {
+    const int tid = threadIdx.x;
+    const uint64_t W = (uint64_t)L.w;
+    const uint64_t e0 = (uint64_t)e * W * (uint64_t)L.h;
+    uint8_t *g0 = Planes::gray(ws, L, e, 0);
+    const size_t gp0 = (size_t)L.gray_pitch[0];
+    uint32_t *h0 = sm.h01[0][tid >> 5];
+    constexpr int kGroups = kTileRows * (kTileCols / 16);
+    constexpr int kPer = kGroups / kPyrThreads;
+    uint4 raw[kPer][3];
+    bool ok[kPer];
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        const int grp = tid + k * kPyrThreads;
+        const int r = grp >> 4, c = (grp & 15) << 4;
+        ok[k] = r < rows && c < cols;
+        if (ok[k]) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(images + 3 * (e0 + (uint64_t)(y0 + r) * W + x0 + c));
+            raw[k][0] = __ldcs(src);
+            raw[k][1] = __ldcs(src + 1);
+            raw[k][2] = __ldcs(src + 2);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        if (!ok[k]) continue;
+        const int grp = tid + k * kPyrThreads;
+        const int r = grp >> 4, c = (grp & 15) << 4;
+        uint32_t g[16];
+        const uint4 v = gray16(raw[k][0], raw[k][1], raw[k][2], g);
+        *reinterpret_cast<uint4 *>(sm.lv + r * kTileCols + c) = v;
+        *reinterpret_cast<uint4 *>(g0 + (size_t)(y0 + r) * gp0 + x0 + c) = v;
+        hist_group(h0, g, v, 0, 16);
+    }
+}
+
+// Any W: the tile row's pixels are a flat run [p0, p0 + cols) that starts
+// anywhere inside a 16-pixel group, so groups are clipped to it.
+__device__ __forceinline__ void tile_level0_general(const uint8_t *__restrict__ images, const mtb_layout_t &L,
+                                                    uint8_t *ws, int e, int y0, int x0, int rows, int cols,
+                                                    PyrShared &sm) {
+    const int tid = threadIdx.x;
+    const uint64_t W = (uint64_t)L.w;
+    const uint64_t plane_px = W * (uint64_t)L.h;
+    const uint64_t total_px = plane_px * (uint64_t)L.n;
+    const uint64_t e0 = (uint64_t)e * plane_px;
+    uint32_t *h0 = sm.h01[0][tid >> 5];
+    for (int s = tid; s < kTileRows * kGroupsPerRow; s += kPyrThreads) {
+        const int r = s / kGroupsPerRow;
+        const int j = s - r * kGroupsPerRow;
+        if (r >= rows) continue;
+        const uint64_t p0 = e0 + (uint64_t)(y0 + r) * W + x0;
+        const uint64_t gp = ((p0 >> 4) + j) << 4;
+        if (gp >= p0 + cols) continue;
+        uint32_t g[16];
+        uint4 v;
+        if (gp + 16 <= total_px) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(images + 3 * gp);
+            v = gray16(__ldcs(src), __ldcs(src + 1), __ldcs(src + 2), g);
+        } else {  // the buffer's last group: pixels past its end are not read
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                g[q] = 0;
+                if (gp + q < total_px) {
+                    const uint8_t *p = images + 3 * (gp + q);
+                    g[q] = luma(p[0], p[1], p[2]);
+                }
+            }
+            v.x = g[0] | (g[1] << 8) | (g[2] << 16) | (g[3] << 24);
+            v.y = g[4] | (g[5] << 8) | (g[6] << 16) | (g[7] << 24);
+            v.z = g[8] | (g[9] << 8) | (g[10] << 16) | (g[11] << 24);
+            v.w = g[12] | (g[13] << 8) | (g[14] << 16) | (g[15] << 24);
+        }
+        const int c0 = (int)((int64_t)gp - (int64_t)p0);  // tile column of pixel 0 of the group; may be < 0
+        const int qa = max(0, -c0), qb = min(16, cols - c0);
+        uint8_t *row = sm.lv + r * kTileCols;
+        if (qa == 0 && qb == 16 && (c0 & 15) == 0) {
+            *reinterpret_cast<uint4 *>(row + c0) = v;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 16; ++q)
+                if (q >= qa && q < qb) row[c0 + q] = (uint8_t)g[q];
+        }
+        hist_group(h0, g, v, qa, qb);
+    }
+}
+
+// Level 0 of the tile from shared memory to global (16-byte stores); used when
+// the level-0 groups were clipped and written byte by byte.
+__device__ __forceinline__ void tile_store_level0(const mtb_layout_t &L, uint8_t *ws, int e, int y0, int x0,
+                                                  int rows, int cols, const PyrShared &sm) {
+    uint8_t *g0 = Planes::gray(ws, L, e, 0);
+    const size_t gp0 = (size_t)L.gray_pitch[0];
+    for (int s = threadIdx.x; s < kTileRows * (kTileCols / 16); s += kPyrThreads) {
+        const int r = s >> 4;
+        const int c = (s & 15) << 4;
+        if (r < rows && c < cols)
+            *reinterpret_cast<uint4 *>(g0 + (size_t)(y0 + r) * gp0 + x0 + c) =
+                *reinterpret_cast<const uint4 *>(sm.lv + r * kTileCols + c);
+    }
+}
+
+// ---- levels 1 and 2 of one tile in one pass ----
+// Thread u takes level-2 pixels (r2, c2..c2+1): level-1 pixels rows 2r2, 2r2+1,
+// columns 2c2..2c2+3, from level-0 rows 4r2..4r2+3, columns 4c2..4c2+7.  Level 1
+// goes to global only; level 2 also to shared memory for levels 3..5.
+__device__ __forceinline__ void tile_levels12(const mtb_layout_t &L, uint8_t *ws, int e, int y0, int x0, int K,
+                                              PyrShared &sm) {
+    static_assert((kTileRows / 4) * (kTileCols / 8) == kPyrThreads, "one level-2 pixel pair per thread");
+    const int u = threadIdx.x;
+    const int r2 = u / (kTileCols / 8), c2 = (u % (kTileCols / 8)) * 2;
+    const uint8_t *src = sm.lv + (4 * r2) * kTileCols + 4 * c2;
+    const uint2 a0 = *reinterpret_cast<const uint2 *>(src);
+    const uint2 a1 = *reinterpret_cast<const uint2 *>(src + kTileCols);
+    const uint2 a2 = *reinterpret_cast<const uint2 *>(src + 2 * kTileCols);
+    const uint2 a3 = *reinterpret_cast<const uint2 *>(src + 3 * kTileCols);
+    const uint32_t w1a = __byte_perm(shrink2(a0.x, a1.x), shrink2(a0.y, a1.y), 0x6420u);  // level-1 row 2r2
+    const uint32_t w1b = __byte_perm(shrink2(a2.x, a3.x), shrink2(a2.y, a3.y), 0x6420u);  // level-1 row 2r2+1
+    {
+        const int W1 = L.width[1], H1 = L.height[1];
+        const int gp1 = L.gray_pitch[1];
+        uint8_t *g1 = Planes::gray(ws, L, e, 1);
+        uint32_t *h1 = sm.h01[1][threadIdx.x >> 5];
+        const int xl = (x0 >> 1) + 2 * c2;
+#pragma unroll
+        for (int rr = 0; rr < 2; ++rr) {
+            const int yl = (y0 >> 1) + 2 * r2 + rr;
+            const uint32_t w = rr ? w1b : w1a;
+            if (yl < H1) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (xl + q < W1) atomicAdd(h1 + ((w >> (8 * q)) & 0xffu), 1u);
+                if (xl < gp1) *reinterpret_cast<uint32_t *>(g1 + (size_t)yl * gp1 + xl) = w;
+            }
+        }
+    }
+    if (K < 2) return;
+    const uint32_t p2 = shrink2(w1a, w1b);                     // [p0, 0, p1, 0] bytes
+    const uint16_t w2 = (uint16_t)__byte_perm(p2, 0u, 0x4420u);  // p0 | p1 << 8
+    *reinterpret_cast<uint16_t *>(sm.lv + lv_offset(2) + r2 * (kTileCols >> 2) + c2) = w2;
+    const int W2 = L.width[2], H2 = L.height[2];
+    const int gp2 = L.gray_pitch[2];
+    const int yl = (y0 >> 2) + r2, xl = (x0 >> 2) + c2;
+    if (yl < H2) {
+        if (xl < W2) atomicAdd(sm.hs[0] + (w2 & 0xffu), 1u);
+        if (xl + 1 < W2) atomicAdd(sm.hs[0] + (w2 >> 8), 1u);
+        if (xl < gp2) *reinterpret_cast<uint16_t *>(Planes::gray(ws, L, e, 2) + (size_t)yl * gp2 + xl) = w2;
+    }
+}
+
+// ---- levels 3..K of one tile, by one warp, from level 2 in shared memory ----
+__device__ __forceinline__ void tile_levels_tail(const mtb_layout_t &L, uint8_t *ws, int e, int y0, int x0, int K,
+                                                 PyrShared &sm) {
+    const int lane = threadIdx.x & 31;
+    for (int l = 3; l <= K; ++l) {
+        const uint8_t *prev = sm.lv + lv_offset(l - 1);
+        const int ppitch = kTileCols >> (l - 1);
+        uint8_t *cur = sm.lv + lv_offset(l);
+        const int cpitch = kTileCols >> l;
+        const int upr = cpitch >> 2;  // 4-pixel units per row
+        const int units = (kTileRows >> l) * upr;
+        const int yl0 = y0 >> l, xl0 = x0 >> l;
+        const int Wl = L.width[l], Hl = L.height[l];
+        const int gpl = L.gray_pitch[l];
+        uint32_t *hl = sm.hs[l - 2];
+        for (int u = lane; u < units; u += 32) {
+            const int r = u / upr;
+            const int c = (u - r * upr) << 2;
+            const uint2 a = *reinterpret_cast<const uint2 *>(prev + (2 * r) * ppitch + 2 * c);
+            const uint2 b = *reinterpret_cast<const uint2 *>(prev + (2 * r + 1) * ppitch + 2 * c);
+            const uint32_t out = __byte_perm(shrink2(a.x, b.x), shrink2(a.y, b.y), 0x6420u);
+            *reinterpret_cast<uint32_t *>(cur + r * cpitch + c) = out;
+            const int yl = yl0 + r, xl = xl0 + c;
+            if (yl < Hl) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (xl + q < Wl) atomicAdd(hl + ((out >> (8 * q)) & 0xffu), 1u);
+                if (xl < gpl) *reinterpret_cast<uint32_t *>(Planes::gray(ws, L, e, l) + (size_t)yl * gpl + xl) = out;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// Adds the CTA's histograms of exposure e to the global ones, clears them and
+// counts the CTA's ntiles tiles of e as done.  The CTA that completes the
+// exposure's last tile computes the medians of levels 0..K (Sec. III-A).
+__device__ void flush_exposure(const mtb_layout_t &L, uint8_t *ws, int e, int ntiles, int tiles_per_exp, int K,
+                               PyrShared &sm) {
+    const int tid = threadIdx.x;
+    __syncthreads();
+    for (int l = 0; l <= K; ++l) {
+        uint32_t *gh = Planes::hist(ws, L, e, l);
+        const int v = tid;  // kPyrThreads == 256 bins
+        uint32_t sum = 0;
+        if (l <= 1) {
+#pragma unroll
+            for (int w = 0; w < kPyrWarps; ++w) {
+                sum += sm.h01[l][w][v];
+                sm.h01[l][w][v] = 0;
+            }
+        } else {
+            sum = sm.hs[l - 2][v];
+            sm.hs[l - 2][v] = 0;
+        }
+        if (sum) atomicAdd(gh + v, sum);
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+        const int old = atomicAdd(Ctr::tiles(ws, L, e), ntiles);
+        sm.last = old + ntiles == tiles_per_exp;
+    }
+    __syncthreads();
+    if (sm.last) {
+        __threadfence();
+        const int warp = tid >> 5;
+        if (warp <= K) {
+            const int m = warp_median<true>(Planes::hist(ws, L, e, warp));
+            if ((tid & 31) == 0) *Planes::median(ws, L, e, warp) = m;
+        }
+        cta_signal(Ctr::pyr_ready(ws, L, e));  // gray planes, histograms and medians of e are complete
+    }
+    __syncthreads();
+}
+
+}  // namespace
+}  // namespace mtb

@@ -39,7 +39,10 @@ def run_stages(mtb, images, levels, tol, ref):
 
 
 def check_stack(mtb, oracle, images, levels, tol, ref, maps=True):
-    """Stage-by-stage parity of one stack; returns the oracle's result."""
+    """Stage-by-stage parity of one stack, then the one-call (engine) path;
+    returns the oracle's result."""
+    import torch
+
     n, h, w, _ = images.shape
     ws, shifts, errs, lsh = run_stages(mtb, images, levels, tol, ref)
     imgs = images.cpu().numpy()
@@ -63,4 +66,10 @@ def check_stack(mtb, oracle, images, levels, tol, ref, maps=True):
     assert np.array_equal(errs.cpu().numpy().view(np.uint32), want["level_errs"]), "level errors"
     assert np.array_equal(lsh.cpu().numpy(), want["level_shifts"]), "level shifts"
     assert np.array_equal(shifts.cpu().numpy(), want["shifts"]), "shifts"
+    # the one-call path: the whole alignment in the engine's persistent launch
+    e_shifts, e_errs, e_lsh = mtb.align_stack(images, levels, tol, ref, level_outputs=True)
+    torch.cuda.synchronize()
+    assert np.array_equal(e_errs.cpu().numpy().view(np.uint32), want["level_errs"]), "engine level errors"
+    assert np.array_equal(e_lsh.cpu().numpy(), want["level_shifts"]), "engine level shifts"
+    assert np.array_equal(e_shifts.cpu().numpy(), want["shifts"]), "engine shifts"
     return want

@@ -102,7 +102,7 @@ def test_layout_invariants(mtb_lib, n, w, h, levels):
     regions.append((lay.median_offset, lay.median_offset + n * levels * 4))
     regions.append((lay.base_offset, lay.base_offset + n * levels * 8))
     regions.append((lay.shift_offset, lay.shift_offset + n * levels * 8))
-    regions.append((lay.counter_offset, lay.counter_offset + (n * (levels + 2) + 16) * 4))
+    regions.append((lay.counter_offset, lay.counter_offset + (n * (2 * levels + 4) + 16) * 4))
     regions.append((lay.table_offset, lay.table_offset + n * 1280 * 4))
     regions.append((lay.status_offset, lay.status_offset + 16))
     regions.sort()
