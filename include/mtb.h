@@ -256,6 +256,76 @@ int mtb_align_stack_noalloc(const uint8_t *images, int n_exposures, int w, int h
                             int noise_tol, int ref_idx, int32_t *shifts_out,
                             uint32_t *level_errs_out, int32_t *level_shifts_out, void *stream);
 
+/* ---- Serving: continuous admission of jobs under a device-memory budget ----
+ * Sec. III-B copies each exposure of a stack to the GPU once and aligns it
+ * there; a server does that for a stream of independent stacks held in host
+ * memory.  It owns one device arena of budget_bytes, `slots` compute streams
+ * and `copy_streams` copy streams, and one worker thread.  A submitted job
+ * waits in arrival order until a slot is free and the arena can hold the job's
+ * images, workspace and shifts (mtb_job_bytes); it is then admitted -- also
+ * while other jobs are still on the GPU -- and its copy in (split over the copy
+ * streams, in admission order), alignment and copy out are enqueued.  Jobs on
+ * different slots overlap on the GPU; each job's pyramids and bitmaps stay in
+ * the arena until its shifts are out, and its memory then returns to the arena.
+ * Every job's shifts are exactly those of mtb_align_stack_ex on the same
+ * stack, whatever else runs beside it. */
+#define MTB_SERVER_MAX_SLOTS 64
+#define MTB_SERVER_MAX_COPY_STREAMS 8
+#define MTB_SERVER_STATS 9
+
+typedef struct mtb_server_config {
+    size_t budget_bytes;  /* device arena, >= 1 MiB (allocated by mtb_server_create) */
+    int slots;            /* jobs on the GPU at most, 1..MTB_SERVER_MAX_SLOTS */
+    int copy_streams;     /* streams each job's copy in is split over, 1..MTB_SERVER_MAX_COPY_STREAMS */
+    int max_pending;      /* jobs waiting for admission at most (0 = no limit) */
+} mtb_server_config_t;
+
+typedef struct mtb_job {
+    const uint8_t *host_images;  /* host [n][h][w][3] uint8, valid until the job completes;
+                                    pinned memory lets the copy overlap other work */
+    int n_exposures, w, h, levels, noise_tol, ref_idx;  /* as for mtb_align_stack */
+    int32_t *host_shifts_out;    /* host int32 [n][2], written when the job completes */
+} mtb_job_t;
+
+typedef struct mtb_server mtb_server_t;
+
+/* Device bytes a job is charged against the budget: its images, workspace and
+ * shifts (= mtb_host_workspace_bytes); 0 if the job is invalid.  Host only. */
+size_t mtb_job_bytes(const mtb_job_t *job);
+
+/* Checks the configuration (MTB_ERR_INVALID_ARG before any CUDA call), then
+ * allocates the arena on the current device (MTB_ERR_OOM if it cannot), the
+ * streams and a pinned result area per slot, and starts the worker. */
+int mtb_server_create(const mtb_server_config_t *config, mtb_server_t **out);
+
+/* Queues a job; *job_id receives its id.  MTB_ERR_INVALID_ARG for an invalid
+ * job; MTB_ERR_BUSY if the job is larger than the whole budget or max_pending
+ * jobs are already waiting (back-pressure: nothing is queued). */
+int mtb_server_submit(mtb_server_t *server, const mtb_job_t *job, uint64_t *job_id);
+
+/* 1 while the job waits or runs, else its final status (MTB_OK, or an
+ * MTB_ERR_* code such as MTB_ERR_TIMEOUT from the device-side waits);
+ * MTB_ERR_INVALID_ARG for an unknown id.  Does not block. */
+int mtb_server_poll(mtb_server_t *server, uint64_t job_id);
+
+/* Blocks until the job completes, returns its final status and forgets the id.
+ * times_ms (NULL or double[2]) receives the latency from submission to the
+ * shifts being in host_shifts_out, and the part of it spent waiting for
+ * admission. */
+int mtb_server_wait(mtb_server_t *server, uint64_t job_id, double *times_ms);
+
+/* Holds (paused != 0) or resumes admission; queued jobs stay queued. */
+int mtb_server_pause(mtb_server_t *server, int paused);
+
+/* values[0..8]: jobs admitted, completed, refused, failed; jobs waiting now,
+ * running now; arena bytes in use now; peak arena bytes in use; peak jobs
+ * running at once.  n_values >= MTB_SERVER_STATS. */
+int mtb_server_stats(mtb_server_t *server, uint64_t *values, int n_values);
+
+/* Resumes admission, waits until every submitted job has completed, then
+ * stops the worker and frees everything.  NULL is ignored. */
+void mtb_server_destroy(mtb_server_t *server);
+
 #ifdef __cplusplus
 }
 #endif

@@ -71,6 +71,24 @@ class StackDesc(ctypes.Structure):
     ]
 
 
+class ServerConfig(ctypes.Structure):
+    """Mirror of mtb_server_config_t."""
+
+    _fields_ = [("budget_bytes", ctypes.c_size_t), ("slots", ctypes.c_int), ("copy_streams", ctypes.c_int),
+                ("max_pending", ctypes.c_int)]
+
+
+class Job(ctypes.Structure):
+    """Mirror of mtb_job_t."""
+
+    _fields_ = [
+        ("host_images", ctypes.c_void_p),
+        ("n_exposures", ctypes.c_int), ("w", ctypes.c_int), ("h", ctypes.c_int), ("levels", ctypes.c_int),
+        ("noise_tol", ctypes.c_int), ("ref_idx", ctypes.c_int),
+        ("host_shifts_out", ctypes.c_void_p),
+    ]
+
+
 def library_path() -> str:
     return LIB_PATH
 
@@ -106,6 +124,14 @@ def lib():
             "mtb_batch_config": (I, [P, ctypes.POINTER(ctypes.c_int), I]),
             "mtb_batch_status": (I, [P, P]),
             "mtb_batch_destroy": (None, [P]),
+            "mtb_job_bytes": (S, [ctypes.POINTER(Job)]),
+            "mtb_server_create": (I, [ctypes.POINTER(ServerConfig), ctypes.POINTER(ctypes.c_void_p)]),
+            "mtb_server_submit": (I, [P, ctypes.POINTER(Job), ctypes.POINTER(ctypes.c_uint64)]),
+            "mtb_server_poll": (I, [P, ctypes.c_uint64]),
+            "mtb_server_wait": (I, [P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]),
+            "mtb_server_pause": (I, [P, I]),
+            "mtb_server_stats": (I, [P, ctypes.POINTER(ctypes.c_uint64), I]),
+            "mtb_server_destroy": (None, [P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -372,6 +398,85 @@ class Batch:
         if getattr(self, "_h", None):
             lib().mtb_batch_destroy(self._h)
             self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+SERVER_STATS = ("admitted", "completed", "refused", "failed", "pending", "running", "bytes_in_use", "peak_bytes",
+                "peak_running")
+
+
+def job_bytes(n: int, w: int, h: int, levels: int, noise_tol: int = 4, ref_idx: int = 0) -> int:
+    """Device bytes a serving job of this shape is charged (0 if invalid)."""
+    j = Job(1 << 20, n, w, h, levels, noise_tol, ref_idx, 1 << 20)
+    return int(lib().mtb_job_bytes(ctypes.byref(j)))
+
+
+class Server:
+    """Continuous serving of alignment jobs under a device-memory budget
+    (mtb_server_* of the C ABI).  Jobs are stacks in host memory (uint8 CPU
+    tensors [n, h, w, 3], pinned for overlapped copies); the native worker admits
+    them in arrival order as slots and arena memory free up."""
+
+    def __init__(self, budget_bytes: int, slots: int = 8, copy_streams: int = 1, max_pending: int = 0):
+        cfg = ServerConfig(int(budget_bytes), int(slots), int(copy_streams), int(max_pending))
+        handle = ctypes.c_void_p()
+        _check(lib().mtb_server_create(ctypes.byref(cfg), ctypes.byref(handle)), "mtb_server_create")
+        self._h = handle
+        self._jobs = {}
+
+    def submit(self, images, levels: int, noise_tol: int = 4, ref_idx: int = 0, out=None) -> int:
+        """Queues one stack; returns the job id.  `out` (int32 CPU tensor [n, 2])
+        receives the shifts when the job completes.  Raises MtbError with
+        MTB_ERR_BUSY when the server refuses the job (back-pressure)."""
+        import torch
+
+        if images.device.type != "cpu" or images.dtype != torch.uint8 or not images.is_contiguous():
+            raise ValueError("images must be a contiguous uint8 CPU tensor [n, h, w, 3]")
+        n, w, h = _dims(images)
+        if out is None:
+            out = torch.empty((n, 2), dtype=torch.int32)
+        job = Job(images.data_ptr(), n, w, h, int(levels), int(noise_tol), int(ref_idx), out.data_ptr())
+        jid = ctypes.c_uint64()
+        _check(lib().mtb_server_submit(self._h, ctypes.byref(job), ctypes.byref(jid)), "mtb_server_submit")
+        self._jobs[jid.value] = (images, out)
+        return jid.value
+
+    def poll(self, job_id: int) -> int:
+        return int(lib().mtb_server_poll(self._h, job_id))
+
+    def wait(self, job_id: int):
+        """Blocks until the job completes; returns (shifts, latency_ms, queue_ms).
+        Raises MtbError if the job failed."""
+        t = (ctypes.c_double * 2)()
+        rc = lib().mtb_server_wait(self._h, job_id, t)
+        _, out = self._jobs.pop(job_id, (None, None))
+        _check(rc, "mtb_server_wait")
+        return out, t[0], t[1]
+
+    def pause(self, paused: bool = True):
+        _check(lib().mtb_server_pause(self._h, int(bool(paused))), "mtb_server_pause")
+
+    def stats(self) -> dict:
+        v = (ctypes.c_uint64 * len(SERVER_STATS))()
+        _check(lib().mtb_server_stats(self._h, v, len(SERVER_STATS)), "mtb_server_stats")
+        return dict(zip(SERVER_STATS, (int(x) for x in v)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().mtb_server_destroy(self._h)
+            self._h = None
+            self._jobs.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
     def __del__(self):
         try:

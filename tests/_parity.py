@@ -39,8 +39,9 @@ def run_stages(mtb, images, levels, tol, ref):
 
 
 def check_stack(mtb, oracle, images, levels, tol, ref, maps=True):
-    """Stage-by-stage parity of one stack, then the one-call (engine) path;
-    returns the oracle's result."""
+    """Stage-by-stage parity of one stack, then the one-call path
+    (mtb_align_stack_ex, the three stages chained on one stream); returns the
+    oracle's result."""
     import torch
 
     n, h, w, _ = images.shape
@@ -66,10 +67,11 @@ def check_stack(mtb, oracle, images, levels, tol, ref, maps=True):
     assert np.array_equal(errs.cpu().numpy().view(np.uint32), want["level_errs"]), "level errors"
     assert np.array_equal(lsh.cpu().numpy(), want["level_shifts"]), "level shifts"
     assert np.array_equal(shifts.cpu().numpy(), want["shifts"]), "shifts"
-    # the one-call path: the whole alignment in the engine's persistent launch
+    # the one-call path: the same kernels, launched back to back with programmatic
+    # dependent launch between the stages
     e_shifts, e_errs, e_lsh = mtb.align_stack(images, levels, tol, ref, level_outputs=True)
     torch.cuda.synchronize()
-    assert np.array_equal(e_errs.cpu().numpy().view(np.uint32), want["level_errs"]), "engine level errors"
-    assert np.array_equal(e_lsh.cpu().numpy(), want["level_shifts"]), "engine level shifts"
-    assert np.array_equal(e_shifts.cpu().numpy(), want["shifts"]), "engine shifts"
+    assert np.array_equal(e_errs.cpu().numpy().view(np.uint32), want["level_errs"]), "one-call level errors"
+    assert np.array_equal(e_lsh.cpu().numpy(), want["level_shifts"]), "one-call level shifts"
+    assert np.array_equal(e_shifts.cpu().numpy(), want["shifts"]), "one-call shifts"
     return want
