@@ -106,7 +106,7 @@ __device__ __noinline__ void pyr_item(const StackDesc &d, int k, EngineShared &s
         if (!d.aligned) tile_store_level0(L, d.ws, e, y0, x0, rows, cols, sm.pyr);
         if (K >= 1) tile_levels12(L, d.ws, e, y0, x0, K, sm.pyr);
         __syncthreads();
-        if (K >= 3 && (threadIdx.x >> 5) == (t & (kPyrWarps - 1))) tile_levels_tail(L, d.ws, e, y0, x0, K, sm.pyr);
+        if (K >= 3) tile_block_tail(L, d.ws, e, y0, x0, K, sm.pyr);
     }
     flush_exposure(L, d.ws, e, t1 - t0, d.tiles_per_exp, K, sm.pyr);
 }

@@ -123,12 +123,12 @@ cudaError_t launch_engine_single(const mtb_layout_t &L, const uint8_t *images, u
 // dependent accesses with pdl_wait().  The first kernel of a call is launched
 // without it, so it starts only after all earlier work in the stream.
 template <typename... KArgs, typename... Args>
-cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, bool after_previous,
-                     Args... args) {
+cudaError_t launch_k_smem(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t dyn_smem, cudaStream_t s,
+                          bool after_previous, Args... args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
     cfg.blockDim = block;
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = dyn_smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -136,6 +136,12 @@ cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream
     cfg.attrs = attr;
     cfg.numAttrs = after_previous ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, bool after_previous,
+                     Args... args) {
+    return launch_k_smem(kernel, grid, block, 0, s, after_previous, args...);
 }
 
 }  // namespace mtb

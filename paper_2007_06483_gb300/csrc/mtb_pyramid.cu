@@ -13,8 +13,8 @@
 // written (gray levels).
 //
 // Instruction budget: at HBM speed the pass has about 17 thread-instructions per
-// pixel, so the gray conversion uses two byte dot products (dp4a) per pixel on
-// byte-permuted RGB words, gray is packed with byte permutes, the 2x2 shrink is
+// pixel, so the gray conversion uses two two-way dot products per pixel on the
+// RGB words as loaded, gray is packed with byte permutes, the 2x2 shrink is
 // done on 16-bit lanes, and a 16-pixel group of one value adds to the histogram
 // with a single shared atomic (saturated regions would otherwise serialise 32
 // lanes on one bin).
@@ -65,9 +65,9 @@ k_pyramid(const uint8_t *__restrict__ images, const mtb_layout_t L, uint8_t *__r
         if (!kAligned) tile_store_level0(L, ws, e, y0, x0, rows, cols, sm);
         if (K >= 1) tile_levels12(L, ws, e, y0, x0, K, sm);
         __syncthreads();
-        // levels 3..5 by one warp (a different one per tile) while the others
-        // start the next tile, which only writes level 0 of the shared buffer
-        if (K >= 3 && (tid >> 5) == (t & (kPyrWarps - 1))) tile_levels_tail(L, ws, e, y0, x0, K, sm);
+        // levels 3..5, a 32-column block per warp; the next tile's level 0 only
+        // writes level 0 of the shared buffer
+        if (K >= 3) tile_block_tail(L, ws, e, y0, x0, K, sm);
         ++done;
     }
     if (cur_e >= 0) {
@@ -91,22 +91,22 @@ cudaError_t launch_pyramid(const uint8_t *images, const mtb_layout_t &L, uint8_t
     const long long per_exp = (long long)tiles_x * tiles_y;
     const long long total = per_exp * L.n;
     if (total > 0x7fffffffLL) return cudaErrorInvalidValue;
-    const bool aligned = (L.w % 16) == 0;
-    int &nb = g_pyr_blocks_per_sm[aligned ? 1 : 0];
-    if (nb == 0) {
-        int v = 0;
-        cudaError_t err = aligned ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_pyramid<true>, kPyrThreads, 0)
-                                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_pyramid<false>, kPyrThreads, 0);
-        if (err != cudaSuccess) return err;
-        nb = v > 0 ? v : 1;
-    }
-    const long long cap = (long long)device_sm_count() * nb;
-    const int grid = (int)(total < cap ? total : cap);
     // histograms and counters are adjacent (layout): clear both in one launch
     const int words = (int)((L.counter_offset - L.hist_offset) / 4) + pyramid_counter_words(L);
     cudaError_t err = launch_k(k_clear, dim3((words + 1023) / 1024 < 64 ? (words + 1023) / 1024 : 64), dim3(256), s,
                                false, reinterpret_cast<uint32_t *>(ws + L.hist_offset), words);
     if (err != cudaSuccess) return err;
+    const bool aligned = (L.w % 16) == 0;
+    int &nb = g_pyr_blocks_per_sm[aligned ? 1 : 0];
+    if (nb == 0) {
+        int v = 0;
+        err = aligned ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_pyramid<true>, kPyrThreads, 0)
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_pyramid<false>, kPyrThreads, 0);
+        if (err != cudaSuccess) return err;
+        nb = v > 0 ? v : 1;
+    }
+    const long long cap = (long long)device_sm_count() * nb;
+    const int grid = (int)(total < cap ? total : cap);
     if (aligned)
         return launch_k(k_pyramid<true>, dim3(grid), dim3(kPyrThreads), s, true, images, L, ws, tiles_x, (int)per_exp,
                         (int)total);

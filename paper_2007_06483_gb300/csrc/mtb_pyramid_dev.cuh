@@ -23,36 +23,33 @@ struct PyrShared {
     int last;
 };
 
-// Q14 luma weights split into high and low bytes: w = 256 * hi + lo, so two
-// byte dot products give the weighted sum exactly.
-constexpr uint32_t kWHi = 19u | (37u << 8) | (7u << 16);
-constexpr uint32_t kWLo = 35u | (145u << 8) | (76u << 16);
-static_assert(19 * 256 + 35 == 4899 && 37 * 256 + 145 == 9617 && 7 * 256 + 76 == 1868, "Q14 weight split");
-
-// Gray of the pixel whose R, G, B are bytes 0..2 (lo3) or 1..3 (hi3) of a word.
-__device__ __forceinline__ uint32_t luma_lo3(uint32_t w) {
-    return (__dp4a(w, kWHi, 0u) * 256u + __dp4a(w, kWLo, 8192u)) >> 14;
-}
-__device__ __forceinline__ uint32_t luma_hi3(uint32_t w) {
-    return (__dp4a(w, kWHi << 8, 0u) * 256u + __dp4a(w, kWLo << 8, 8192u)) >> 14;
-}
-
-// 4 pixels = 12 RGB bytes in words w0..w2 -> their gray values and the packed word.
-__device__ __forceinline__ uint32_t gray4(uint32_t w0, uint32_t w1, uint32_t w2, uint32_t *g) {
-    g[0] = luma_lo3(w0);
-    g[1] = luma_lo3(__byte_perm(w0, w1, 0x0543));  // bytes 3, 4, 5
-    g[2] = luma_lo3(__byte_perm(w1, w2, 0x0432));  // bytes 6, 7, 8
-    g[3] = luma_hi3(w2);                          // bytes 9, 10, 11
-    return __byte_perm(__byte_perm(g[0], g[1], 0x3340), __byte_perm(g[2], g[3], 0x3340), 0x5410);
+// 4 pixels = 12 RGB bytes in words w0..w2 -> their gray values and the packed
+// word, by two-way dot products (16-bit weights times 2 bytes),
+// with the weights and rounding term scaled by 4: 4 * (4899 R + 9617 G +
+// 1868 B + 8192) < 2^24, and its byte 2 is (4899 R + 9617 G + 1868 B + 8192)
+// >> 14, so the gray value is read off byte 2 with no shift.  Each pixel's
+// three bytes are addressed where they lie (bytes 0..2, 3..5, 6..8, 9..11).
+constexpr uint32_t kRG4 = (4899u * 4) | ((9617u * 4) << 16), kGB4 = (9617u * 4) | ((1868u * 4) << 16);
+constexpr uint32_t kB04 = 1868u * 4, k0R4 = (4899u * 4) << 16, kBias4 = 8192u * 4;
+__device__ __forceinline__ uint32_t gray4_dp2(uint32_t w0, uint32_t w1, uint32_t w2, uint32_t *g) {
+    const uint32_t p0 = __dp2a_hi(kB04, w0, __dp2a_lo(kRG4, w0, kBias4));  // R G | B .
+    const uint32_t p1 = __dp2a_hi(k0R4, w0, __dp2a_lo(kGB4, w1, kBias4));  // . R | G B
+    const uint32_t p2 = __dp2a_lo(kB04, w2, __dp2a_hi(kRG4, w1, kBias4));  // R G | B .
+    const uint32_t p3 = __dp2a_hi(kGB4, w2, __dp2a_lo(k0R4, w2, kBias4));  // . R | G B
+    g[0] = __byte_perm(p0, 0u, 0x4442u);
+    g[1] = __byte_perm(p1, 0u, 0x4442u);
+    g[2] = __byte_perm(p2, 0u, 0x4442u);
+    g[3] = __byte_perm(p3, 0u, 0x4442u);
+    return __byte_perm(__byte_perm(p0, p1, 0x7362u), __byte_perm(p2, p3, 0x7362u), 0x5410u);
 }
 
 // 16 pixels of one 48-byte group -> gray values and 4 packed words.
 __device__ __forceinline__ uint4 gray16(const uint4 &a, const uint4 &b, const uint4 &c, uint32_t (&g)[16]) {
     uint4 v;
-    v.x = gray4(a.x, a.y, a.z, g + 0);
-    v.y = gray4(a.w, b.x, b.y, g + 4);
-    v.z = gray4(b.z, b.w, c.x, g + 8);
-    v.w = gray4(c.y, c.z, c.w, g + 12);
+    v.x = gray4_dp2(a.x, a.y, a.z, g + 0);
+    v.y = gray4_dp2(a.w, b.x, b.y, g + 4);
+    v.z = gray4_dp2(b.z, b.w, c.x, g + 8);
+    v.w = gray4_dp2(c.y, c.z, c.w, g + 12);
     return v;
 }
 
@@ -229,34 +226,27 @@ __device__ __forceinline__ void tile_levels12(const mtb_layout_t &L, uint8_t *ws
     }
 }
 
-// ---- levels 3..K of one tile, by one warp, from level 2 in shared memory ----
-__device__ __forceinline__ void tile_levels_tail(const mtb_layout_t &L, uint8_t *ws, int e, int y0, int x0, int K,
-                                                 PyrShared &sm) {
-    const int lane = threadIdx.x & 31;
-    for (int l = 3; l <= K; ++l) {
-        const uint8_t *prev = sm.lv + lv_offset(l - 1);
-        const int ppitch = kTileCols >> (l - 1);
-        uint8_t *cur = sm.lv + lv_offset(l);
-        const int cpitch = kTileCols >> l;
-        const int upr = cpitch >> 2;  // 4-pixel units per row
-        const int units = (kTileRows >> l) * upr;
-        const int yl0 = y0 >> l, xl0 = x0 >> l;
-        const int Wl = L.width[l], Hl = L.height[l];
-        const int gpl = L.gray_pitch[l];
-        uint32_t *hl = sm.hs[l - 2];
-        for (int u = lane; u < units; u += 32) {
-            const int r = u / upr;
-            const int c = (u - r * upr) << 2;
-            const uint2 a = *reinterpret_cast<const uint2 *>(prev + (2 * r) * ppitch + 2 * c);
-            const uint2 b = *reinterpret_cast<const uint2 *>(prev + (2 * r + 1) * ppitch + 2 * c);
-            const uint32_t out = __byte_perm(shrink2(a.x, b.x), shrink2(a.y, b.y), 0x6420u);
-            *reinterpret_cast<uint32_t *>(cur + r * cpitch + c) = out;
-            const int yl = yl0 + r, xl = xl0 + c;
-            if (yl < Hl) {
+// ---- levels 3..K of one tile, from level 2 in shared memory ----
+// Level-5 pixel w of the tile sums the tile's 32-column block w, so warp w
+// builds levels 3..5 of block w (16, 4 and 1 pixels): every warp does the same
+// small share and none holds the others up at the next barrier.
+__device__ __forceinline__ void tile_block_tail(const mtb_layout_t &L, uint8_t *ws, int e, int y0, int x0, int K,
+                                                PyrShared &sm) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (xl + q < Wl) atomicAdd(hl + ((out >> (8 * q)) & 0xffu), 1u);
-                if (xl < gpl) *reinterpret_cast<uint32_t *>(Planes::gray(ws, L, e, l) + (size_t)yl * gpl + xl) = out;
+    for (int l = 3; l <= kTileLog2; ++l) {
+        if (l > K) break;
+        const int side = kTileRows >> l;                // block side at level l: 4, 2, 1
+        const int ppitch = kTileCols >> (l - 1), pitch = kTileCols >> l;
+        if (lane < side * side) {
+            const int r = lane / side, c = w * side + lane % side;
+            const uint8_t *a = sm.lv + lv_offset(l - 1) + (2 * r) * ppitch + 2 * c;
+            const uint32_t px = ((uint32_t)a[0] + a[1] + a[ppitch] + a[ppitch + 1] + 2u) >> 2;
+            sm.lv[lv_offset(l) + r * pitch + c] = (uint8_t)px;
+            const int yl = (y0 >> l) + r, xl = (x0 >> l) + c;
+            if (yl < L.height[l]) {
+                if (xl < L.width[l]) atomicAdd(sm.hs[l - 2] + px, 1u);
+                if (xl < L.gray_pitch[l]) Planes::gray(ws, L, e, l)[(size_t)yl * L.gray_pitch[l] + xl] = (uint8_t)px;
             }
         }
         __syncwarp();

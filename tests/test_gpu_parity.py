@@ -37,6 +37,13 @@ SHAPES = [
     (1001, 333, 4, 2, 1),
     (4100, 300, 3, 2, 0),
     (9000, 100, 2, 3, 2),
+    # widths that are a multiple of 16 (the tensor-copy pyramid): a 16-wide image
+    # narrower than one copy box, ragged 32x32 tiles in x and y, deep levels
+    (16, 16, 4, 2, 0),
+    (48, 37, 5, 3, 1),
+    (176, 1000, 7, 2, 0),
+    (2064, 999, 8, 3, 2),
+    (4000, 31, 5, 2, 1),
 ]
 
 
