@@ -135,7 +135,8 @@ int mtb_align_stack_ex(const uint8_t *images, int n_exposures, int w, int h, int
                        void *workspace, size_t workspace_bytes, void *stream);
 
 /* Stage 1 (Sec. III-A gray conversion and pyramid, Sec. III-B histograms):
- * clears the histogram and counter areas, then writes the gray planes,
+ * clears every area after the bit planes (histograms, counters, errors,
+ * medians, bases, shifts, window tables, status), then writes the gray planes,
  * histograms and medians of levels 0..tile_levels-1 into the workspace. */
 int mtb_build_pyramids(const uint8_t *images, int n_exposures, int w, int h, int levels,
                        void *workspace, size_t workspace_bytes, void *stream);

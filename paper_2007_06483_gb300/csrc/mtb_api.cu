@@ -105,7 +105,7 @@ int run_all(const uint8_t *images, const mtb_layout_t &L, int tol, int ref, uint
     if (rc != MTB_OK) return rc;
     rc = cuda_status(launch_bitmaps(L, tol, ws, s, true));
     if (rc != MTB_OK) return rc;
-    return cuda_status(launch_search(L, ref, ws, shifts_out, level_errs_out, level_shifts_out, s, true));
+    return cuda_status(launch_search(L, ref, ws, shifts_out, level_errs_out, level_shifts_out, s, true, true));
 }
 
 bool misaligned(const void *p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) != 0; }

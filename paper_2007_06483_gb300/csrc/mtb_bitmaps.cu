@@ -24,8 +24,11 @@
 namespace mtb {
 namespace {
 
+// CTAs are numbered deep levels first, then the tile levels from the coarsest
+// to level 0, each over all exposures: the planes a chained search needs first
+// (its coarse levels) are finished first.
 __global__ void __launch_bounds__(kBitThreads)
-k_bitmaps(const mtb_layout_t L, uint8_t *__restrict__ ws, int tol, int deep_ctas, int chunks_per_exp) {
+k_bitmaps(const mtb_layout_t L, uint8_t *__restrict__ ws, int tol, int deep_ctas) {
     __shared__ uint32_t s_hist[256];
     __shared__ int s_med;
     pdl_trigger();
@@ -34,11 +37,16 @@ k_bitmaps(const mtb_layout_t L, uint8_t *__restrict__ ws, int tol, int deep_ctas
         deep_levels(L, ws, tol, blockIdx.x, s_hist, &s_med);
         return;
     }
-    const int item = blockIdx.x - deep_ctas;
-    const int e = item / chunks_per_exp;
-    int l, c;
-    bitmap_chunk_of(L, item - e * chunks_per_exp, kBitWordsPerCta, &l, &c);
-    bitmap_chunk(L, ws, tol, e, l, c, kBitWordsPerCta, &s_med);
+    int item = blockIdx.x - deep_ctas;
+    int l = L.tile_levels - 1;
+    for (; l > 0; --l) {
+        const int per_level = bitmap_chunks(L, l, kBitWordsPerCta) * L.n;
+        if (item < per_level) break;
+        item -= per_level;
+    }
+    const int ch = bitmap_chunks(L, l, kBitWordsPerCta);
+    const int e = item / ch;
+    bitmap_chunk(L, ws, tol, e, l, item - e * ch, kBitWordsPerCta, &s_med);
 }
 
 }  // namespace
@@ -52,8 +60,7 @@ cudaError_t launch_bitmaps(const mtb_layout_t &L, int noise_tol, uint8_t *ws, cu
     const int deep = L.levels > L.tile_levels ? L.n : 0;
     const long long grid = deep + per_exp * L.n;
     if (grid > 0x7fffffffLL) return cudaErrorInvalidValue;
-    return launch_k(k_bitmaps, dim3((unsigned)grid), dim3(kBitThreads), s, chained, L, ws, noise_tol, deep,
-                    (int)per_exp);
+    return launch_k(k_bitmaps, dim3((unsigned)grid), dim3(kBitThreads), s, chained, L, ws, noise_tol, deep);
 }
 
 }  // namespace mtb

@@ -104,11 +104,15 @@ int check_stack_args(int n, int w, int h, int levels, int noise_tol, int ref_idx
 cudaError_t launch_pyramid(const uint8_t *images, const mtb_layout_t &L, uint8_t *ws, cudaStream_t s);
 cudaError_t launch_bitmaps(const mtb_layout_t &L, int noise_tol, uint8_t *ws, cudaStream_t s, bool chained);
 int coarse_start_level(const mtb_layout_t &L);
+// `overlap` (only directly after launch_bitmaps of the same call, on a workspace
+// the same call's launch_pyramid cleared): the search starts while the bitmaps
+// are being packed and waits per bit plane.
 cudaError_t launch_search(const mtb_layout_t &L, int ref_idx, uint8_t *ws, int32_t *shifts_out,
-                          uint32_t *level_errs_out, int32_t *level_shifts_out, cudaStream_t s, bool chained);
+                          uint32_t *level_errs_out, int32_t *level_shifts_out, cudaStream_t s, bool chained,
+                          bool overlap = false);
 cudaError_t launch_search_ex(const mtb_layout_t &L, int ref_idx, uint8_t *ws, int32_t *shifts_out,
                              uint32_t *level_errs_out, int32_t *level_shifts_out, cudaStream_t s, bool chained,
-                             unsigned long long timeout_ns, int withhold_pair);
+                             unsigned long long timeout_ns, int withhold_pair, bool overlap = false);
 
 int device_sm_count();
 

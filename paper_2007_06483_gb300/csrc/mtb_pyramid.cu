@@ -91,10 +91,16 @@ cudaError_t launch_pyramid(const uint8_t *images, const mtb_layout_t &L, uint8_t
     const long long per_exp = (long long)tiles_x * tiles_y;
     const long long total = per_exp * L.n;
     if (total > 0x7fffffffLL) return cudaErrorInvalidValue;
-    // histograms and counters are adjacent (layout): clear both in one launch
-    const int words = (int)((L.counter_offset - L.hist_offset) / 4) + pyramid_counter_words(L);
-    cudaError_t err = launch_k(k_clear, dim3((words + 1023) / 1024 < 64 ? (words + 1023) / 1024 : 64), dim3(256), s,
-                               false, reinterpret_cast<uint32_t *>(ws + L.hist_offset), words);
+    // everything after the bit planes (histograms, counters, errors, medians,
+    // bases, shifts, window tables, status) is small and adjacent: one launch
+    // clears it, so that a search chained to this pyramid needs no clearing of
+    // its own and can start while the bitmaps are still being packed
+    const long long words = (long long)(L.total_bytes - L.hist_offset) / 4;
+    const long long cap = 4ll * device_sm_count();
+    const long long blocks = (words + 1023) / 1024 < cap ? (words + 1023) / 1024 : cap;
+    if (words > 0x7fffffffLL) return cudaErrorInvalidValue;
+    cudaError_t err = launch_k(k_clear, dim3((unsigned)blocks), dim3(256), s, false,
+                               reinterpret_cast<uint32_t *>(ws + L.hist_offset), (int)words);
     if (err != cudaSuccess) return err;
     const bool aligned = (L.w % 16) == 0;
     int &nb = g_pyr_blocks_per_sm[aligned ? 1 : 0];
@@ -105,8 +111,8 @@ cudaError_t launch_pyramid(const uint8_t *images, const mtb_layout_t &L, uint8_t
         if (err != cudaSuccess) return err;
         nb = v > 0 ? v : 1;
     }
-    const long long cap = (long long)device_sm_count() * nb;
-    const int grid = (int)(total < cap ? total : cap);
+    const long long cap_p = (long long)device_sm_count() * nb;
+    const int grid = (int)(total < cap_p ? total : cap_p);
     if (aligned)
         return launch_k(k_pyramid<true>, dim3(grid), dim3(kPyrThreads), s, true, images, L, ws, tiles_x, (int)per_exp,
                         (int)total);

@@ -35,12 +35,18 @@
 namespace mtb {
 namespace {
 
+// kOverlap: the launch directly follows the bitmap pass of the same call, whose
+// clearing was done by the pyramid stage; the search then starts while the
+// bitmaps are still being packed, and every item waits for the planes it reads
+// (their completion counters, acquired; weak loads afterwards) instead of for
+// the whole previous launch.
+template <bool kOverlap>
 __global__ void __launch_bounds__(kSearchThreads, 4)
 k_search(const mtb_layout_t L, uint8_t *__restrict__ ws, const SearchPlan P) {
     __shared__ SearchShared sm;
     const int tid = threadIdx.x;
     pdl_trigger();
-    pdl_wait();  // bit planes and cleared counters come from the previous launches
+    if (!kOverlap) pdl_wait();  // bit planes and cleared counters come from the previous launches
     int32_t *head = Ctr::queue(ws, L);
     for (;;) {
         if (tid == 0) sm.item = atomicAdd(head, 1);
@@ -50,7 +56,7 @@ k_search(const mtb_layout_t L, uint8_t *__restrict__ ws, const SearchPlan P) {
         if (it >= P.total_items) break;
         const int n_window = P.pairs * P.window_items;
         if (it < n_window) {
-            window_item<false>(L, ws, P, it, sm);
+            window_item<kOverlap>(L, ws, P, it, sm);
         } else if (it < n_window + P.pairs) {
             resolve_item(L, ws, P, it - n_window, sm);
         } else if (it == P.total_items - 1) {
@@ -59,7 +65,7 @@ k_search(const mtb_layout_t L, uint8_t *__restrict__ ws, const SearchPlan P) {
             int l = P.lc - 1;
             while (l > 0 && it >= P.first_item[l - 1]) --l;
             const int rel = it - P.first_item[l];
-            shift_item<false>(L, ws, P, rel / P.chunks[l], l, rel % P.chunks[l], sm);
+            shift_item<kOverlap>(L, ws, P, rel / P.chunks[l], l, rel % P.chunks[l], sm);
         }
     }
 }
@@ -83,7 +89,7 @@ __global__ void k_clear_search(const mtb_layout_t L, uint8_t *__restrict__ ws, i
     pdl_wait();
 }
 
-int g_search_blocks_per_sm = 0;
+int g_search_blocks_per_sm[2] = {0, 0};
 
 }  // namespace
 
@@ -147,27 +153,33 @@ void plan_search(const mtb_layout_t &L, int ref_idx, long long cap, int32_t *shi
 
 cudaError_t launch_search_ex(const mtb_layout_t &L, int ref_idx, uint8_t *ws, int32_t *shifts_out,
                              uint32_t *level_errs_out, int32_t *level_shifts_out, cudaStream_t s, bool chained,
-                             unsigned long long timeout_ns, int withhold_pair) {
-    if (g_search_blocks_per_sm == 0) {
+                             unsigned long long timeout_ns, int withhold_pair, bool overlap) {
+    int &nb = g_search_blocks_per_sm[overlap ? 1 : 0];
+    if (nb == 0) {
         int v = 0;
-        cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_search, kSearchThreads, 0);
+        cudaError_t err = overlap
+                              ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_search<true>, kSearchThreads, 0)
+                              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_search<false>, kSearchThreads, 0);
         if (err != cudaSuccess) return err;
-        g_search_blocks_per_sm = v > 0 ? v : 1;
+        nb = v > 0 ? v : 1;
     }
-    const long long cap = (long long)device_sm_count() * g_search_blocks_per_sm;
+    const long long cap = (long long)device_sm_count() * nb;
     SearchPlan P;
     plan_search(L, ref_idx, cap, shifts_out, level_errs_out, level_shifts_out, timeout_ns, withhold_pair, &P);
     if (P.total_items < 0) return cudaErrorInvalidValue;
     const int grid = (int)(P.total_items < cap ? P.total_items : cap);
+    if (overlap)  // the pyramid stage of the same call cleared the search's areas
+        return launch_k(k_search<true>, dim3(grid), dim3(kSearchThreads), s, true, L, ws, P);
     cudaError_t err = launch_k(k_clear_search, dim3(1), dim3(1024), s, chained, L, ws, ref_idx);
     if (err != cudaSuccess) return err;
-    return launch_k(k_search, dim3(grid), dim3(kSearchThreads), s, true, L, ws, P);
+    return launch_k(k_search<false>, dim3(grid), dim3(kSearchThreads), s, true, L, ws, P);
 }
 
 cudaError_t launch_search(const mtb_layout_t &L, int ref_idx, uint8_t *ws, int32_t *shifts_out,
-                          uint32_t *level_errs_out, int32_t *level_shifts_out, cudaStream_t s, bool chained) {
+                          uint32_t *level_errs_out, int32_t *level_shifts_out, cudaStream_t s, bool chained,
+                          bool overlap) {
     return launch_search_ex(L, ref_idx, ws, shifts_out, level_errs_out, level_shifts_out, s, chained,
-                            kSearchTimeoutNs, -1);
+                            kSearchTimeoutNs, -1, overlap);
 }
 
 }  // namespace mtb

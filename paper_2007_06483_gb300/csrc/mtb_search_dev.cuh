@@ -344,8 +344,10 @@ __device__ void shift_item(const mtb_layout_t &L, uint8_t *ws, const SearchPlan 
     const int tid = threadIdx.x;
     const int i = p < P.ref ? p : p + 1;
     if (tid == 0) {
-        int bx = 0, by = 0, ok = 1;
-        if (l + 1 < L.levels) {
+        int bx = 0, by = 0;
+        // the planes first: they are usually ready before the level below is
+        int ok = wait_bits<kEng>(ws, L, P, i, l);
+        if (ok && l + 1 < L.levels) {
             ok = wait_at_least(done_ctr(ws, L, p, l + 1), level_target(P, l + 1), status_word(ws, L), P.timeout_ns);
             if (ok) {
                 uint32_t e1[9];
@@ -364,7 +366,6 @@ __device__ void shift_item(const mtb_layout_t &L, uint8_t *ws, const SearchPlan 
                 }
             }
         }
-        if (ok) ok = wait_bits<kEng>(ws, L, P, i, l);
         if (ok && c == 0) {
             int32_t *b0 = Planes::base(ws, L, i, l);
             b0[0] = bx;
