@@ -78,6 +78,11 @@ class Oracle:
         lib.orc_check_args.restype = I
         lib.orc_align_stack.argtypes = [P, I, I, I, I, I, I, P, P, P]
         lib.orc_align_stack.restype = I
+        lib.orc_apply_shifts.argtypes = [P, I, I, I, P, I, P]
+        lib.orc_align_stack_chain.argtypes = [P, I, I, I, I, I, I, P, P, P]
+        lib.orc_align_stack_chain.restype = I
+        lib.orc_align_quadrants.argtypes = [P, I, I, I, I, I, I, I, P, P]
+        lib.orc_align_quadrants.restype = I
         lib.orc_candidate.argtypes = [I, ctypes.POINTER(I), ctypes.POINTER(I)]
         lib.orc_candidate.restype = I
         self.lib = lib
@@ -195,6 +200,52 @@ class Oracle:
         return {"shifts": shifts, "level_errs": errs, "level_shifts": lsh}
 
 
+    def apply_shifts(self, images, shifts, fill: int = 0) -> np.ndarray:
+        """Each exposure of [n, h, w, 3] moved by its (sx, sy); fill 0: zeros,
+        1: nearest edge pixel, where the source lies outside."""
+        images = _u8(images)
+        n, h, w, c = images.shape
+        assert c == 3
+        shifts = np.ascontiguousarray(shifts, dtype=np.int32).reshape(n, 2)
+        out = np.empty_like(images)
+        self.lib.orc_apply_shifts(_ptr(images), n, w, h, _ptr(shifts), int(fill), _ptr(out))
+        return out
+
+    def align_stack_chain(self, images, levels: int, noise_tol: int, ref_idx: int) -> dict:
+        """Consecutive-chain alignment: each exposure against its neighbour towards
+        ref_idx, shifts composed along the chain.  Same outputs as align_stack
+        (per-level rows hold the neighbour pair's values)."""
+        images = _u8(images)
+        n, h, w, c = images.shape
+        assert c == 3
+        shifts = np.zeros((n, 2), np.int32)
+        errs = np.zeros((n, levels, 9), np.uint32)
+        lsh = np.zeros((n, levels, 2), np.int32)
+        rc = self.lib.orc_align_stack_chain(_ptr(images), n, w, h, levels, int(noise_tol), int(ref_idx),
+                                            _ptr(shifts), _ptr(errs), _ptr(lsh))
+        if rc == -1:
+            raise ValueError("invalid arguments")
+        if rc != 0:
+            raise MemoryError("oracle ran out of host memory")
+        return {"shifts": shifts, "level_errs": errs, "level_shifts": lsh}
+
+    def align_quadrants(self, images, levels: int, noise_tol: int, ref_idx: int, rot_tol: int = 1) -> dict:
+        """Per-quadrant alignment (quadrants TL, TR, BL, BR) and the rotation flag.
+        Returns dict(quad_shifts [n,4,2] int32, flags [n] int32)."""
+        images = _u8(images)
+        n, h, w, c = images.shape
+        assert c == 3
+        qs = np.zeros((n, 4, 2), np.int32)
+        flags = np.zeros(n, np.int32)
+        rc = self.lib.orc_align_quadrants(_ptr(images), n, w, h, levels, int(noise_tol), int(ref_idx),
+                                          int(rot_tol), _ptr(qs), _ptr(flags))
+        if rc == -1:
+            raise ValueError("invalid arguments")
+        if rc != 0:
+            raise MemoryError("oracle ran out of host memory")
+        return {"quad_shifts": qs, "flags": flags}
+
+
 def default() -> Oracle:
     """The oracle built from oracle/mtb_oracle.c."""
     global _lib
@@ -242,3 +293,15 @@ def check_args(n, w, h, levels, tol, ref):
 
 def align_stack(images, levels, noise_tol, ref_idx):
     return default().align_stack(images, levels, noise_tol, ref_idx)
+
+
+def apply_shifts(images, shifts, fill=0):
+    return default().apply_shifts(images, shifts, fill)
+
+
+def align_stack_chain(images, levels, noise_tol, ref_idx):
+    return default().align_stack_chain(images, levels, noise_tol, ref_idx)
+
+
+def align_quadrants(images, levels, noise_tol, ref_idx, rot_tol=1):
+    return default().align_quadrants(images, levels, noise_tol, ref_idx, rot_tol)

@@ -256,3 +256,157 @@ done:
     free(best);
     return rc;
 }
+
+/* ---- After the alignment, and the paper's other readings of "pairwise" ---- */
+
+/* Moves each exposure's RGB by the shift the search found for it: the operator
+ * S of the search (Sec. III-B moves the second image's maps), applied to the
+ * image itself, out(x, y) = in(x - sx, y - sy) per channel.  A pixel whose
+ * source lies outside the image gets 0 (fill 0) or the nearest edge pixel
+ * (fill 1).  shifts: [n][2]; out: [n][h][w][3], not overlapping images. */
+void orc_apply_shifts(const uint8_t *images, int n, int w, int h, const int32_t *shifts, int fill, uint8_t *out)
+{
+    for (int e = 0; e < n; ++e) {
+        const uint8_t *src = images + (size_t)e * w * h * 3;
+        uint8_t *dst = out + (size_t)e * w * h * 3;
+        for (int y = 0; y < h; ++y) {
+            for (int x = 0; x < w; ++x) {
+                long long xs = (long long)x - shifts[2 * e + 0];
+                long long ys = (long long)y - shifts[2 * e + 1];
+                int inside = xs >= 0 && xs < w && ys >= 0 && ys < h;
+                uint8_t *p = dst + ((size_t)y * w + x) * 3;
+                if (!inside && fill == 0) {
+                    p[0] = p[1] = p[2] = 0;
+                    continue;
+                }
+                if (xs < 0) xs = 0;
+                if (xs >= w) xs = w - 1;
+                if (ys < 0) ys = 0;
+                if (ys >= h) ys = h - 1;
+                const uint8_t *q = src + ((size_t)ys * w + xs) * 3;
+                p[0] = q[0];
+                p[1] = q[1];
+                p[2] = q[2];
+            }
+        }
+    }
+}
+
+/* Consecutive-chain alignment.  Sec. II notes that each exposure can be
+ * compared with its neighbours; Sec. III-B still takes n - 1 pair alignments.
+ * Here exposure i != ref is searched against its neighbour towards ref
+ * (i + 1 below ref, i - 1 above), and the translations add up along the chain:
+ * shift[i] = pair shift of (neighbour, i) + shift[neighbour], shift[ref] = 0.
+ * level_errs and level_shifts rows hold the pair (neighbour, i) values.  Same
+ * arguments and return codes as orc_align_stack. */
+int orc_align_stack_chain(const uint8_t *images, int n, int w, int h, int levels, int tol,
+                          int ref, int32_t *shifts, uint32_t *level_errs, int32_t *level_shifts)
+{
+    if (orc_check_args(n, w, h, levels, tol, ref) != 0) return -1;
+    long total = orc_level_offset(w, h, levels);
+    long npix0 = (long)w * h;
+    uint8_t *gray = malloc((size_t)total);
+    uint32_t *hist = malloc(sizeof(uint32_t) * 256 * (size_t)levels);
+    int32_t *med = malloc(sizeof(int32_t) * (size_t)levels);
+    uint8_t *tb = malloc((size_t)total * n);
+    uint8_t *eb = malloc((size_t)total * n);
+    uint32_t *errs = malloc(sizeof(uint32_t) * 9 * (size_t)levels);
+    int32_t *best = malloc(sizeof(int32_t) * 2 * (size_t)levels);
+    int32_t *pair = malloc(sizeof(int32_t) * 2 * (size_t)n);
+    int rc = 0;
+    if (!gray || !hist || !med || !tb || !eb || !errs || !best || !pair) {
+        rc = -2;
+        goto done;
+    }
+    for (int e = 0; e < n; ++e)
+        orc_exposure_maps(images + (size_t)e * npix0 * 3, w, h, levels, tol, gray, hist, med,
+                          tb + (size_t)e * total, eb + (size_t)e * total);
+    for (int i = 0; i < n; ++i) {
+        if (i == ref) {
+            memset(errs, 0, sizeof(uint32_t) * 9 * (size_t)levels);
+            memset(best, 0, sizeof(int32_t) * 2 * (size_t)levels);
+        } else {
+            int nb = i < ref ? i + 1 : i - 1;
+            orc_search_pair(tb + (size_t)nb * total, eb + (size_t)nb * total,
+                            tb + (size_t)i * total, eb + (size_t)i * total,
+                            w, h, levels, errs, best);
+        }
+        pair[2 * i + 0] = best[0];
+        pair[2 * i + 1] = best[1];
+        if (level_errs) memcpy(level_errs + (size_t)i * levels * 9, errs, sizeof(uint32_t) * 9 * (size_t)levels);
+        if (level_shifts) memcpy(level_shifts + (size_t)i * levels * 2, best, sizeof(int32_t) * 2 * (size_t)levels);
+    }
+    shifts[2 * ref + 0] = 0;
+    shifts[2 * ref + 1] = 0;
+    for (int i = ref - 1; i >= 0; --i) {
+        shifts[2 * i + 0] = pair[2 * i + 0] + shifts[2 * (i + 1) + 0];
+        shifts[2 * i + 1] = pair[2 * i + 1] + shifts[2 * (i + 1) + 1];
+    }
+    for (int i = ref + 1; i < n; ++i) {
+        shifts[2 * i + 0] = pair[2 * i + 0] + shifts[2 * (i - 1) + 0];
+        shifts[2 * i + 1] = pair[2 * i + 1] + shifts[2 * (i - 1) + 1];
+    }
+done:
+    free(gray);
+    free(hist);
+    free(med);
+    free(tb);
+    free(eb);
+    free(errs);
+    free(best);
+    free(pair);
+    return rc;
+}
+
+/* Ward's test for a rotation between exposures, which the paper's Sec. II
+ * recalls: split every exposure into four quadrants and align each quadrant
+ * stack on its own.  Quadrant q = 2 * qy + qx (top-left, top-right,
+ * bottom-left, bottom-right) is the floor(w/2) x floor(h/2) block at
+ * (qx * floor(w/2), qy * floor(h/2)); each quadrant stack is aligned directly
+ * to ref.  quad_shifts: [n][4][2].  flags[i] = 1 when the four quadrant
+ * shifts of exposure i spread by more than rot_tol pixels in x or in y (a pure
+ * translation moves every quadrant alike), else 0.  Returns as
+ * orc_align_stack; -1 also when the quadrants are too small for `levels`. */
+int orc_align_quadrants(const uint8_t *images, int n, int w, int h, int levels, int tol, int ref,
+                        int rot_tol, int32_t *quad_shifts, int32_t *flags)
+{
+    const int wq = w / 2, hq = h / 2;
+    if (orc_check_args(n, wq, hq, levels, tol, ref) != 0 || rot_tol < 0) return -1;
+    uint8_t *sub = malloc((size_t)n * wq * hq * 3);
+    int32_t *sh = malloc(sizeof(int32_t) * 2 * (size_t)n);
+    int rc = 0;
+    if (!sub || !sh) {
+        rc = -2;
+        goto done;
+    }
+    for (int q = 0; q < 4; ++q) {
+        const int x0 = (q & 1) * wq, y0 = (q >> 1) * hq;
+        for (int e = 0; e < n; ++e)
+            for (int y = 0; y < hq; ++y)
+                memcpy(sub + (((size_t)e * hq + y) * wq) * 3,
+                       images + (((size_t)e * h + y0 + y) * w + x0) * 3, (size_t)wq * 3);
+        rc = orc_align_stack(sub, n, wq, hq, levels, tol, ref, sh, NULL, NULL);
+        if (rc != 0) goto done;
+        for (int e = 0; e < n; ++e) {
+            quad_shifts[(e * 4 + q) * 2 + 0] = sh[2 * e + 0];
+            quad_shifts[(e * 4 + q) * 2 + 1] = sh[2 * e + 1];
+        }
+    }
+    for (int e = 0; e < n; ++e) {
+        int flag = 0;
+        for (int c = 0; c < 2; ++c) {
+            int lo = quad_shifts[(e * 4) * 2 + c], hi = lo;
+            for (int q = 1; q < 4; ++q) {
+                int v = quad_shifts[(e * 4 + q) * 2 + c];
+                if (v < lo) lo = v;
+                if (v > hi) hi = v;
+            }
+            if (hi - lo > rot_tol) flag = 1;
+        }
+        flags[e] = flag;
+    }
+done:
+    free(sub);
+    free(sh);
+    return rc;
+}

@@ -233,3 +233,99 @@ def pin_constant_and_identical(orc, seed=7):
     res = orc.align_stack(same, 4, 4, 1)
     assert not res["shifts"].any() and not res["level_shifts"].any()
     assert not res["level_errs"][:, :, 0].any()
+
+
+# ---- after the alignment, and the other readings of "pairwise" --------------
+def pin_apply_scipy(orc, seed=8):
+    """Moving the RGB by an integer shift is a nearest-order translation:
+    scipy's ndimage.shift with mode 'constant' (fill 0) / 'nearest' (edge)
+    computes the same image."""
+    from scipy import ndimage
+
+    rng = np.random.default_rng(seed)
+    for h, w in ((7, 9), (16, 5), (1, 1), (33, 40)):
+        n = 3
+        img = rng.integers(0, 256, (n, h, w, 3), dtype=np.uint8)
+        xs = [0, 1, -1, w - 1, -(w - 1), w, -w, w + 3, 1000, -5]
+        ys = [0, 1, -1, h, -h - 2, 3]
+        for fill, mode in ((0, "constant"), (1, "nearest")):
+            sh = np.array([[rng.choice(xs), rng.choice(ys)] for _ in range(n)], np.int32)
+            out = orc.apply_shifts(img, sh, fill)
+            for e in range(n):
+                want = ndimage.shift(img[e], (int(sh[e, 1]), int(sh[e, 0]), 0), order=0, mode=mode, cval=0)
+                assert np.array_equal(out[e], want), (h, w, fill, sh[e].tolist())
+
+
+def _stack(seed, w, h, n, levels, ref, shift_range):
+    from paper_2007_06483_gb300 import synth
+
+    spec = synth.small_spec(seed, w, h, n=n, levels=levels, shift_range=shift_range, ref=ref)
+    return synth.make_stack(spec).numpy(), synth.expected_shifts(spec)
+
+
+def pin_chain(orc, seed=9):
+    """Chain mode: with two exposures it is the direct pair; the composed shift
+    of each exposure minus its neighbour's is that pair's own level-0 shift;
+    planted shifts are recovered through the chain."""
+    imgs, _ = _stack(seed, 96, 80, 2, 4, 1, 5)
+    a, b = orc.align_stack(imgs, 4, 4, 1), orc.align_stack_chain(imgs, 4, 4, 1)
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+    imgs, want = _stack(seed + 3, 160, 120, 5, 5, 2, 6)  # every planted component is non-zero
+    assert all((want[i] != 0).all() for i in (0, 1, 3, 4))
+    res = orc.align_stack_chain(imgs, 5, 4, 2)
+    sh, lsh = res["shifts"], res["level_shifts"]
+    assert not sh[2].any() and not lsh[2].any()
+    for i in range(5):
+        if i != 2:
+            nb = i + 1 if i < 2 else i - 1
+            assert np.array_equal(sh[i] - sh[nb], lsh[i, 0]), i
+    assert np.array_equal(sh, want), (sh.tolist(), want.tolist())
+
+
+def _rotate_nearest(img, deg):
+    """[h, w, 3] image turned by deg about its centre (nearest source pixel,
+    edge replicated): test input only."""
+    h, w = img.shape[:2]
+    t = np.deg2rad(deg)
+    yy, xx = np.mgrid[0:h, 0:w].astype(np.float64)
+    cx, cy = (w - 1) / 2.0, (h - 1) / 2.0
+    xs = np.cos(t) * (xx - cx) + np.sin(t) * (yy - cy) + cx
+    ys = -np.sin(t) * (xx - cx) + np.cos(t) * (yy - cy) + cy
+    xi = np.clip(np.rint(xs), 0, w - 1).astype(np.int64)
+    yi = np.clip(np.rint(ys), 0, h - 1).astype(np.int64)
+    return img[yi, xi]
+
+
+def pin_quadrants(orc, seed=10):
+    """Per-quadrant alignment: quadrant q equals the whole-stack oracle on the
+    numpy-cropped quadrant; a pure translation moves all four quadrants alike
+    (no flag); a rotation moves opposite quadrants in opposite directions
+    (flagged)."""
+    imgs, want = _stack(seed, 258, 194, 3, 4, 1, 4)
+    res = orc.align_quadrants(imgs, 4, 4, 1, 1)
+    hq, wq = 194 // 2, 258 // 2
+    for q in range(4):
+        y0, x0 = (q >> 1) * hq, (q & 1) * wq
+        crop = np.ascontiguousarray(imgs[:, y0:y0 + hq, x0:x0 + wq])
+        assert np.array_equal(res["quad_shifts"][:, q], orc.align_stack(crop, 4, 4, 1)["shifts"]), q
+    for q in range(4):
+        assert np.array_equal(res["quad_shifts"][:, q], want), (q, res["quad_shifts"].tolist())
+    assert not res["flags"].any()
+    base, _ = _stack(seed + 1, 256, 192, 1, 4, 0, 0)
+    rot = np.stack([base[0], _rotate_nearest(base[0], 3.0)])
+    r = orc.align_quadrants(rot, 4, 4, 0, 1)
+    tl, tr, bl, br = (r["quad_shifts"][1, q] for q in range(4))
+    assert r["flags"][1] == 1 and r["flags"][0] == 0, r
+    # a turn about the centre moves each quadrant along the perpendicular of its
+    # offset from the centre: opposite corners move in opposite directions, the
+    # top two alike in x and oppositely in y (signs only: the estimates are coarse)
+    sg = [np.sign(v.astype(np.int64)) for v in (tl, tr, bl, br)]
+    assert all(v.all() for v in sg), r
+    assert (sg[0] == -sg[3]).all() and (sg[1] == -sg[2]).all(), r
+    assert sg[0][0] == sg[1][0] and sg[0][1] == -sg[1][1], r
+    # the flag is "spread > rot_tol": off at rot_tol = spread, on just below it
+    q = r["quad_shifts"][1]
+    spread = int((q.max(axis=0) - q.min(axis=0)).max())
+    assert orc.align_quadrants(rot, 4, 4, 0, spread)["flags"][1] == 0
+    assert orc.align_quadrants(rot, 4, 4, 0, spread - 1)["flags"][1] == 1

@@ -34,6 +34,7 @@ ALL_PINS = [
     P.pin_gray_spot, P.pin_gray_bt601, P.pin_shrink, P.pin_histogram, P.pin_median, P.pin_bitmaps,
     P.pin_shift_error, P.pin_shift_symmetry, P.pin_candidate_order, P.pin_search_rule,
     lambda orc: P.pin_brute_force(orc, make_pair), P.pin_constant_and_identical,
+    P.pin_apply_scipy, P.pin_chain, P.pin_quadrants,
 ]
 
 
@@ -130,6 +131,13 @@ MUTATIONS = {
     "search_no_doubling": ("bx = 2 * best[2 * l + 0];", "bx = best[2 * l + 0];"),
     "search_last_minimum": ("if (e[k] < e[kbest]) kbest = k;", "if (e[k] <= e[kbest]) kbest = k;"),
     "candidate_order": ("{0, -1, 0, 1, -1, 1, -1, 0, 1}", "{0, 1, 0, -1, -1, 1, -1, 0, 1}"),
+    "apply_sign": ("long long xs = (long long)x - shifts[2 * e + 0];", "long long xs = (long long)x + shifts[2 * e + 0];"),
+    "apply_no_fill": ("if (!inside && fill == 0) {", "if (!inside && fill == 2) {"),
+    "chain_wrong_neighbour": ("int nb = i < ref ? i + 1 : i - 1;", "int nb = i < ref ? i - 1 : i + 1;"),
+    "chain_composition_sign": ("shifts[2 * i + 0] = pair[2 * i + 0] + shifts[2 * (i + 1) + 0];",
+                               "shifts[2 * i + 0] = pair[2 * i + 0] - shifts[2 * (i + 1) + 0];"),
+    "quadrant_origin_swapped": ("const int x0 = (q & 1) * wq, y0 = (q >> 1) * hq;", "const int x0 = (q >> 1) * wq, y0 = (q & 1) * hq;"),
+    "quadrant_flag_threshold": ("if (hi - lo > rot_tol) flag = 1;", "if (hi - lo >= rot_tol) flag = 1;"),
 }
 
 
