@@ -134,6 +134,19 @@ int mtb_align_stack_ex(const uint8_t *images, int n_exposures, int w, int h, int
                        uint32_t *level_errs_out, int32_t *level_shifts_out,
                        void *workspace, size_t workspace_bytes, void *stream);
 
+/* Consecutive-chain alignment.  Sec. II recalls that each exposure can be
+ * compared with its neighbours; Sec. III-B still takes n - 1 pair alignments.
+ * Here exposure i != ref_idx is searched against its neighbour towards ref_idx
+ * (i + 1 below it, i - 1 above it) and the translations add up along the chain:
+ * shifts_out[i] = the pair's shift + shifts_out[neighbour], shifts_out[ref] =
+ * (0, 0).  level_errs_out / level_shifts_out rows hold the pair (neighbour, i)
+ * values (level 0 of level_shifts_out is the pair's own shift).  Arguments,
+ * workspace and errors as in mtb_align_stack_ex. */
+int mtb_align_stack_chain(const uint8_t *images, int n_exposures, int w, int h, int levels,
+                          int noise_tol, int ref_idx, int32_t *shifts_out,
+                          uint32_t *level_errs_out, int32_t *level_shifts_out,
+                          void *workspace, size_t workspace_bytes, void *stream);
+
 /* Stage 1 (Sec. III-A gray conversion and pyramid, Sec. III-B histograms):
  * clears every area after the bit planes (histograms, counters, errors,
  * medians, bases, shifts, window tables, status), then writes the gray planes,
@@ -256,6 +269,46 @@ void mtb_batch_destroy(mtb_batch_t *batch);
 int mtb_align_stack_noalloc(const uint8_t *images, int n_exposures, int w, int h, int levels,
                             int noise_tol, int ref_idx, int32_t *shifts_out,
                             uint32_t *level_errs_out, int32_t *level_shifts_out, void *stream);
+
+/* ---- After the alignment: moving the exposures ----------------------------
+ * The search's operator S (Sec. III-B moves the second image's maps by
+ * (sx, sy), 0 outside the image) applied to the RGB exposures themselves:
+ * out_i(x, y) = in_i(x - sx_i, y - sy_i), per channel.  Where the source lies
+ * outside the image the pixel is 0 (MTB_FILL_ZERO) or the nearest edge pixel
+ * (MTB_FILL_EDGE).  The paper stops at the shifts; this is the step after. */
+#define MTB_FILL_ZERO 0
+#define MTB_FILL_EDGE 1
+
+/* images: device [n][h][w][3] uint8, 16-byte aligned; shifts: device int32
+ * [n][2] (e.g. the shifts_out of an alignment on the same stream); out: device
+ * [n][h][w][3] uint8, 16-byte aligned, not overlapping images.  Requires
+ * 1 <= n <= MTB_MAX_EXPOSURES, 1 <= w, h <= MTB_MAX_DIM, fill 0 or 1; any int32
+ * shift is valid (beyond the image the whole exposure is fill).  Enqueues one
+ * kernel on `stream`. */
+int mtb_apply_shifts(const uint8_t *images, int n_exposures, int w, int h, const int32_t *shifts, int fill,
+                     uint8_t *out, void *stream);
+
+/* ---- Rotation test by quadrants --------------------------------------------
+ * Sec. II recalls Ward's test for a rotation between exposures: split each
+ * exposure into four quadrants and align every quadrant stack on its own; a
+ * pure translation moves the four alike.  Quadrant q = 2*qy + qx (top-left,
+ * top-right, bottom-left, bottom-right) is the floor(w/2) x floor(h/2) block at
+ * (qx*floor(w/2), qy*floor(h/2)); each quadrant stack is aligned directly to
+ * ref_idx exactly as mtb_align_stack would align it. */
+
+/* Device workspace of mtb_align_quadrants (0 if the sizes are invalid). */
+size_t mtb_quadrant_workspace_bytes(int n_exposures, int w, int h, int levels);
+
+/* images: device [n][h][w][3] uint8 (16-byte aligned); `levels` must be valid
+ * for the floor(w/2) x floor(h/2) quadrants (other arguments as for
+ * mtb_align_stack).  quad_shifts_out: device int32 [n][4][2]; flags_out: device
+ * int32 [n] or NULL -- 1 where the four quadrant shifts of an exposure spread by
+ * more than rot_tol (>= 0) pixels in x or in y, else 0.  workspace: device,
+ * 256-byte aligned, >= mtb_quadrant_workspace_bytes(...), or NULL to allocate
+ * stream-ordered. */
+int mtb_align_quadrants(const uint8_t *images, int n_exposures, int w, int h, int levels, int noise_tol,
+                        int ref_idx, int rot_tol, int32_t *quad_shifts_out, int32_t *flags_out,
+                        void *workspace, size_t workspace_bytes, void *stream);
 
 /* ---- Serving: continuous admission of jobs under a device-memory budget ----
  * Sec. III-B copies each exposure of a stack to the GPU once and aligns it

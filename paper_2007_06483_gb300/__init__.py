@@ -22,6 +22,8 @@ MTB_ERR_CUDA = -3
 MTB_ERR_TIMEOUT = -4
 MTB_ERR_BUSY = -5
 MTB_MAX_LEVELS = 16
+MTB_FILL_ZERO = 0
+MTB_FILL_EDGE = 1
 
 _lock = threading.Lock()
 _lib = None
@@ -124,6 +126,10 @@ def lib():
             "mtb_batch_config": (I, [P, ctypes.POINTER(ctypes.c_int), I]),
             "mtb_batch_status": (I, [P, P]),
             "mtb_batch_destroy": (None, [P]),
+            "mtb_apply_shifts": (I, [P, I, I, I, P, I, P, P]),
+            "mtb_align_stack_chain": (I, [P, I, I, I, I, I, I, P, P, P, P, S, P]),
+            "mtb_quadrant_workspace_bytes": (S, [I, I, I, I]),
+            "mtb_align_quadrants": (I, [P, I, I, I, I, I, I, I, P, P, P, S, P]),
             "mtb_job_bytes": (S, [ctypes.POINTER(Job)]),
             "mtb_server_create": (I, [ctypes.POINTER(ServerConfig), ctypes.POINTER(ctypes.c_void_p)]),
             "mtb_server_submit": (I, [P, ctypes.POINTER(Job), ctypes.POINTER(ctypes.c_uint64)]),
@@ -227,6 +233,50 @@ def align_stack(images, levels: int, noise_tol: int = 4, ref_idx: int = 0, *, le
     return shifts
 
 
+def align_stack_chain(images, levels: int, noise_tol: int = 4, ref_idx: int = 0, *, level_outputs: bool = False,
+                      workspace=None, out=None, stream=None):
+    """mtb_align_stack_chain: every exposure searched against its neighbour
+    towards ref_idx, shifts composed along the chain.  Returns and outputs as
+    align_stack (per-level rows hold the neighbour pair's values)."""
+    import torch
+
+    n, w, h = _dims(images)
+    dev = images.device
+    shifts = out if out is not None else torch.empty((n, 2), dtype=torch.int32, device=dev)
+    errs = lsh = None
+    if level_outputs:
+        errs = torch.empty((n, levels, 9), dtype=torch.int32, device=dev)  # viewed as uint32
+        lsh = torch.empty((n, levels, 2), dtype=torch.int32, device=dev)
+    ws_ptr, ws_bytes = None, 0
+    if workspace is not None:
+        ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
+    _check(lib().mtb_align_stack_chain(images.data_ptr(), n, w, h, levels, noise_tol, ref_idx, shifts.data_ptr(),
+                                       _ptr(errs), _ptr(lsh), ws_ptr, ws_bytes, _stream(stream)),
+           "mtb_align_stack_chain")
+    if level_outputs:
+        return shifts, errs, lsh
+    return shifts
+
+
+def align_quadrants(images, levels: int, noise_tol: int = 4, ref_idx: int = 0, rot_tol: int = 1, *,
+                    workspace=None, stream=None):
+    """mtb_align_quadrants: per-quadrant alignment (TL, TR, BL, BR) and the
+    rotation flag.  Returns (quad_shifts int32 [n, 4, 2], flags int32 [n]) on
+    the device."""
+    import torch
+
+    n, w, h = _dims(images)
+    dev = images.device
+    qs = torch.empty((n, 4, 2), dtype=torch.int32, device=dev)
+    flags = torch.empty((n,), dtype=torch.int32, device=dev)
+    ws_ptr, ws_bytes = None, 0
+    if workspace is not None:
+        ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
+    _check(lib().mtb_align_quadrants(images.data_ptr(), n, w, h, levels, noise_tol, ref_idx, rot_tol, qs.data_ptr(),
+                                     flags.data_ptr(), ws_ptr, ws_bytes, _stream(stream)), "mtb_align_quadrants")
+    return qs, flags
+
+
 def build_pyramids(images, levels: int, workspace, stream=None):
     n, w, h = _dims(images)
     _check(lib().mtb_build_pyramids(images.data_ptr(), n, w, h, levels, workspace.data_ptr(), workspace.numel(),
@@ -302,6 +352,22 @@ def workspace_views(workspace, n: int, w: int, h: int, levels: int) -> dict:
         "base": area(lay.base_offset, n * levels * 2, torch.int32, (n, levels, 2)),
         "shift": area(lay.shift_offset, n * levels * 2, torch.int32, (n, levels, 2)),
     }
+
+
+def apply_shifts(images, shifts, fill: int = MTB_FILL_ZERO, *, out=None, stream=None):
+    """mtb_apply_shifts: every exposure of images (uint8 CUDA [n, h, w, 3]) moved
+    by its (sx, sy) from shifts (int32 CUDA [n, 2]); fill MTB_FILL_ZERO or
+    MTB_FILL_EDGE.  Returns out ([n, h, w, 3], allocated here if not given)."""
+    import torch
+
+    n, w, h = _dims(images)
+    if shifts.dtype != torch.int32 or shifts.device != images.device or tuple(shifts.shape) != (n, 2):
+        raise ValueError("shifts must be an int32 tensor [n, 2] on the images' device")
+    if out is None:
+        out = torch.empty_like(images)
+    _check(lib().mtb_apply_shifts(images.data_ptr(), n, w, h, shifts.contiguous().data_ptr(), int(fill),
+                                  out.data_ptr(), _stream(stream)), "mtb_apply_shifts")
+    return out
 
 
 _noalloc_fn = None

@@ -100,12 +100,12 @@ int stage_pyramid(const uint8_t *images, const mtb_layout_t &L, uint8_t *ws, cud
 // (lower latency for a single stack than the engine, whose strength is
 // overlapping many stacks in a batch).
 int run_all(const uint8_t *images, const mtb_layout_t &L, int tol, int ref, uint8_t *ws, int32_t *shifts_out,
-            uint32_t *level_errs_out, int32_t *level_shifts_out, cudaStream_t s) {
+            uint32_t *level_errs_out, int32_t *level_shifts_out, cudaStream_t s, bool chain = false) {
     int rc = stage_pyramid(images, L, ws, s);
     if (rc != MTB_OK) return rc;
     rc = cuda_status(launch_bitmaps(L, tol, ws, s, true));
     if (rc != MTB_OK) return rc;
-    return cuda_status(launch_search(L, ref, ws, shifts_out, level_errs_out, level_shifts_out, s, true, true));
+    return cuda_status(launch_search(L, ref, ws, shifts_out, level_errs_out, level_shifts_out, s, true, true, chain));
 }
 
 bool misaligned(const void *p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) != 0; }
@@ -179,6 +179,23 @@ int mtb_align_stack_ex(const uint8_t *images, int n_exposures, int w, int h, int
     rc = acquire(workspace, workspace_bytes, L.total_bytes, s, &ws, &owned);
     if (rc != MTB_OK) return rc;
     rc = run_all(images, L, noise_tol, ref_idx, ws, shifts_out, level_errs_out, level_shifts_out, s);
+    return release(ws, owned, s, rc);
+}
+
+int mtb_align_stack_chain(const uint8_t *images, int n_exposures, int w, int h, int levels, int noise_tol,
+                          int ref_idx, int32_t *shifts_out, uint32_t *level_errs_out, int32_t *level_shifts_out,
+                          void *workspace, size_t workspace_bytes, void *stream) {
+    int rc = check_stack_args(n_exposures, w, h, levels, noise_tol, ref_idx);
+    if (rc != MTB_OK) return rc;
+    if (!images || !shifts_out || misaligned(images, 16)) return MTB_ERR_INVALID_ARG;
+    mtb_layout_t L;
+    compute_layout(n_exposures, w, h, levels, &L);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    uint8_t *ws = nullptr;
+    bool owned = false;
+    rc = acquire(workspace, workspace_bytes, L.total_bytes, s, &ws, &owned);
+    if (rc != MTB_OK) return rc;
+    rc = run_all(images, L, noise_tol, ref_idx, ws, shifts_out, level_errs_out, level_shifts_out, s, true);
     return release(ws, owned, s, rc);
 }
 
@@ -285,6 +302,67 @@ int mtb_align_stack_host(const uint8_t *host_images, int n_exposures, int w, int
     rc = release(base, owned, s, rc);
     if (cudaStreamSynchronize(s) != cudaSuccess && rc == MTB_OK) rc = MTB_ERR_CUDA;
     return rc;
+}
+
+// Quadrant workspace: the four quadrant stacks, one alignment workspace used by
+// the four alignments in turn, and their shifts [4][n][2].
+static int quadrant_layout(int n, int w, int h, int levels, mtb_layout_t *Lq, size_t *quad_stride,
+                           size_t *ws_offset, size_t *shifts_offset, size_t *total) {
+    const int wq = w / 2, hq = h / 2;
+    int rc = compute_layout(n, wq, hq, levels, Lq);
+    if (rc != MTB_OK) return rc;
+    *quad_stride = align_up((size_t)n * wq * hq * 3, 256);
+    *ws_offset = 4 * *quad_stride;
+    *shifts_offset = *ws_offset + align_up(Lq->total_bytes, 256);
+    *total = *shifts_offset + align_up((size_t)4 * n * 2 * sizeof(int32_t), 256);
+    return MTB_OK;
+}
+
+size_t mtb_quadrant_workspace_bytes(int n_exposures, int w, int h, int levels) {
+    mtb_layout_t Lq;
+    size_t stride, wso, so, total;
+    if (w < 2 || h < 2 || quadrant_layout(n_exposures, w, h, levels, &Lq, &stride, &wso, &so, &total) != MTB_OK)
+        return 0;
+    return total;
+}
+
+int mtb_align_quadrants(const uint8_t *images, int n_exposures, int w, int h, int levels, int noise_tol, int ref_idx,
+                        int rot_tol, int32_t *quad_shifts_out, int32_t *flags_out, void *workspace,
+                        size_t workspace_bytes, void *stream) {
+    if (w < 2 || h < 2 || w > MTB_MAX_DIM || h > MTB_MAX_DIM || rot_tol < 0) return MTB_ERR_INVALID_ARG;
+    int rc = check_stack_args(n_exposures, w / 2, h / 2, levels, noise_tol, ref_idx);
+    if (rc != MTB_OK) return rc;
+    if (!images || !quad_shifts_out || misaligned(images, 16)) return MTB_ERR_INVALID_ARG;
+    mtb_layout_t Lq;
+    size_t stride, wso, so, total;
+    quadrant_layout(n_exposures, w, h, levels, &Lq, &stride, &wso, &so, &total);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    uint8_t *base = nullptr;
+    bool owned = false;
+    rc = acquire(workspace, workspace_bytes, total, s, &base, &owned);
+    if (rc != MTB_OK) return rc;
+    int32_t *quad = reinterpret_cast<int32_t *>(base + so);
+    rc = cuda_status(launch_gather_quadrants(images, n_exposures, w, h, base, (long long)stride, s));
+    for (int q = 0; q < 4 && rc == MTB_OK; ++q)
+        rc = run_all(base + q * stride, Lq, noise_tol, ref_idx, base + wso, quad + (size_t)q * n_exposures * 2,
+                     nullptr, nullptr, s);
+    if (rc == MTB_OK)
+        rc = cuda_status(launch_quadrant_flags(quad, n_exposures, rot_tol, quad_shifts_out, flags_out, s));
+    return release(base, owned, s, rc);
+}
+
+int mtb_apply_shifts(const uint8_t *images, int n_exposures, int w, int h, const int32_t *shifts, int fill,
+                     uint8_t *out, void *stream) {
+    if (n_exposures < 1 || n_exposures > MTB_MAX_EXPOSURES || w < 1 || h < 1 || w > MTB_MAX_DIM ||
+        h > MTB_MAX_DIM || (fill != MTB_FILL_ZERO && fill != MTB_FILL_EDGE))
+        return MTB_ERR_INVALID_ARG;
+    if (!images || !shifts || !out || misaligned(images, 16) || misaligned(out, 16) || misaligned(shifts, 4))
+        return MTB_ERR_INVALID_ARG;
+    const uintptr_t bytes = (uintptr_t)n_exposures * w * h * 3;
+    const uintptr_t a = reinterpret_cast<uintptr_t>(images), b = reinterpret_cast<uintptr_t>(out);
+    if (a < b + bytes && b < a + bytes) return MTB_ERR_INVALID_ARG;  // overlapping buffers
+    return cuda_status(launch_apply_shifts(images, n_exposures, w, h, shifts, fill, out,
+                                           static_cast<cudaStream_t>(stream)));
 }
 
 }  // extern "C"

@@ -103,16 +103,24 @@ int check_stack_args(int n, int w, int h, int levels, int noise_tol, int ref_idx
 // dependent launch).  A stage called on its own starts after all earlier work.
 cudaError_t launch_pyramid(const uint8_t *images, const mtb_layout_t &L, uint8_t *ws, cudaStream_t s);
 cudaError_t launch_bitmaps(const mtb_layout_t &L, int noise_tol, uint8_t *ws, cudaStream_t s, bool chained);
+cudaError_t launch_apply_shifts(const uint8_t *images, int n, int w, int h, const int32_t *shifts, int fill,
+                                uint8_t *out, cudaStream_t s);
+cudaError_t launch_gather_quadrants(const uint8_t *images, int n, int w, int h, uint8_t *out, long long quad_stride,
+                                    cudaStream_t s);
+cudaError_t launch_quadrant_flags(const int32_t *quad, int n, int rot_tol, int32_t *out, int32_t *flags,
+                                  cudaStream_t s);
 int coarse_start_level(const mtb_layout_t &L);
 // `overlap` (only directly after launch_bitmaps of the same call, on a workspace
 // the same call's launch_pyramid cleared): the search starts while the bitmaps
-// are being packed and waits per bit plane.
+// are being packed and waits per bit plane.  `chain`: each exposure is searched
+// against its neighbour towards ref and the shifts are composed.
 cudaError_t launch_search(const mtb_layout_t &L, int ref_idx, uint8_t *ws, int32_t *shifts_out,
                           uint32_t *level_errs_out, int32_t *level_shifts_out, cudaStream_t s, bool chained,
-                          bool overlap = false);
+                          bool overlap = false, bool chain = false);
 cudaError_t launch_search_ex(const mtb_layout_t &L, int ref_idx, uint8_t *ws, int32_t *shifts_out,
                              uint32_t *level_errs_out, int32_t *level_shifts_out, cudaStream_t s, bool chained,
-                             unsigned long long timeout_ns, int withhold_pair, bool overlap = false);
+                             unsigned long long timeout_ns, int withhold_pair, bool overlap = false,
+                             bool chain = false);
 
 int device_sm_count();
 

@@ -108,10 +108,12 @@ int coarse_start_level(const mtb_layout_t &L) {
 }
 
 void plan_search(const mtb_layout_t &L, int ref_idx, long long cap, int32_t *shifts_out, uint32_t *level_errs_out,
-                 int32_t *level_shifts_out, unsigned long long timeout_ns, int withhold_pair, SearchPlan *out) {
+                 int32_t *level_shifts_out, unsigned long long timeout_ns, int withhold_pair, SearchPlan *out,
+                 int chain) {
     SearchPlan &P = *out;
     P = SearchPlan{};
     P.ref = ref_idx;
+    P.chain = chain;
     P.pairs = L.n - 1;
     P.lc = coarse_start_level(L);
     P.shifts_out = shifts_out;
@@ -153,7 +155,7 @@ void plan_search(const mtb_layout_t &L, int ref_idx, long long cap, int32_t *shi
 
 cudaError_t launch_search_ex(const mtb_layout_t &L, int ref_idx, uint8_t *ws, int32_t *shifts_out,
                              uint32_t *level_errs_out, int32_t *level_shifts_out, cudaStream_t s, bool chained,
-                             unsigned long long timeout_ns, int withhold_pair, bool overlap) {
+                             unsigned long long timeout_ns, int withhold_pair, bool overlap, bool chain) {
     int &nb = g_search_blocks_per_sm[overlap ? 1 : 0];
     if (nb == 0) {
         int v = 0;
@@ -165,7 +167,8 @@ cudaError_t launch_search_ex(const mtb_layout_t &L, int ref_idx, uint8_t *ws, in
     }
     const long long cap = (long long)device_sm_count() * nb;
     SearchPlan P;
-    plan_search(L, ref_idx, cap, shifts_out, level_errs_out, level_shifts_out, timeout_ns, withhold_pair, &P);
+    plan_search(L, ref_idx, cap, shifts_out, level_errs_out, level_shifts_out, timeout_ns, withhold_pair, &P,
+                chain ? 1 : 0);
     if (P.total_items < 0) return cudaErrorInvalidValue;
     const int grid = (int)(P.total_items < cap ? P.total_items : cap);
     if (overlap)  // the pyramid stage of the same call cleared the search's areas
@@ -177,9 +180,9 @@ cudaError_t launch_search_ex(const mtb_layout_t &L, int ref_idx, uint8_t *ws, in
 
 cudaError_t launch_search(const mtb_layout_t &L, int ref_idx, uint8_t *ws, int32_t *shifts_out,
                           uint32_t *level_errs_out, int32_t *level_shifts_out, cudaStream_t s, bool chained,
-                          bool overlap) {
+                          bool overlap, bool chain) {
     return launch_search_ex(L, ref_idx, ws, shifts_out, level_errs_out, level_shifts_out, s, chained,
-                            kSearchTimeoutNs, -1, overlap);
+                            kSearchTimeoutNs, -1, overlap, chain);
 }
 
 }  // namespace mtb

@@ -9,6 +9,7 @@ namespace mtb {
 // Geometry and queue layout of one search; filled on the host.
 struct SearchPlan {
     int ref, lc, pairs, total_items;
+    int chain;         // 0: every exposure against ref; 1: against its neighbour towards ref
     int window_items;  // window items (row of a level's window x word chunk) of one pair
     int32_t *shifts_out;
     uint32_t *level_errs_out;
@@ -22,7 +23,8 @@ struct SearchPlan {
 };
 
 void plan_search(const mtb_layout_t &L, int ref_idx, long long cap, int32_t *shifts_out, uint32_t *level_errs_out,
-                 int32_t *level_shifts_out, unsigned long long timeout_ns, int withhold_pair, SearchPlan *out);
+                 int32_t *level_shifts_out, unsigned long long timeout_ns, int withhold_pair, SearchPlan *out,
+                 int chain = 0);
 
 namespace {
 
@@ -137,12 +139,19 @@ __device__ __forceinline__ uint2 bit_load(const uint2 *p) {
     return kEng ? ld_weak(p) : __ldg(p);
 }
 
-// Engine only: thread 0 waits until level l of exposures ref and i is packed.
+// The exposure that moving exposure i is searched against: ref itself, or in
+// chain mode its neighbour towards ref.
+__device__ __forceinline__ int pair_ref(const SearchPlan &P, int i) {
+    return P.chain ? (i < P.ref ? i + 1 : i - 1) : P.ref;
+}
+
+// Engine and overlapped search: thread 0 waits until level l of exposure i and
+// of the exposure it is searched against is packed.
 template <bool kEng>
 __device__ __forceinline__ bool wait_bits(uint8_t *ws, const mtb_layout_t &L, const SearchPlan &P, int i, int l) {
     if (!kEng) return true;
     const int target = bitmap_target(L, l, P.bit_chunk_words);
-    return wait_at_least(Ctr::bit_done(ws, L, P.ref, l), target, status_word(ws, L), P.timeout_ns) &&
+    return wait_at_least(Ctr::bit_done(ws, L, pair_ref(P, i), l), target, status_word(ws, L), P.timeout_ns) &&
            wait_at_least(Ctr::bit_done(ws, L, i, l), target, status_word(ws, L), P.timeout_ns);
 }
 
@@ -184,7 +193,7 @@ __device__ void finalize_exposure(const mtb_layout_t &L, uint8_t *ws, const Sear
     int32_t *s0 = Planes::shift(ws, L, i, 0);
     s0[0] = sx;
     s0[1] = sy;
-    if (P.shifts_out) {
+    if (P.shifts_out && !P.chain) {
         P.shifts_out[2 * i] = sx;
         P.shifts_out[2 * i + 1] = sy;
     }
@@ -219,7 +228,7 @@ __device__ void window_row(const mtb_layout_t &L, uint8_t *ws, const SearchPlan 
         if (!sm.ok) return;
     }
     const int hl = L.height[l], bp = L.bits_pitch[l];
-    const uint2 *pr = Planes::bits(ws, L, P.ref, l);
+    const uint2 *pr = Planes::bits(ws, L, pair_ref(P, i), l);
     const uint2 *pi = Planes::bits(ws, L, i, l);
     uint32_t cnt[N];
 #pragma unroll
@@ -383,7 +392,7 @@ __device__ void shift_item(const mtb_layout_t &L, uint8_t *ws, const SearchPlan 
     const int cb = c % P.col_blocks[l], rb = c / P.col_blocks[l];
     const int x = tid % tx, yb = tid / tx;
     const bool active = yb < ty;
-    const uint2 *pr = Planes::bits(ws, L, P.ref, l);
+    const uint2 *pr = Planes::bits(ws, L, pair_ref(P, i), l);
     const uint2 *pi = Planes::bits(ws, L, i, l);
     const int w = cb * tx + x;
     const int t = -bx - 1;
@@ -431,6 +440,20 @@ __device__ void final_item(const mtb_layout_t &L, uint8_t *ws, const SearchPlan 
     __syncthreads();
     if (!sm.ok) return;
     for (int e = threadIdx.x; e < L.n; e += kSearchThreads) finalize_exposure(L, ws, P, e);
+    if (!P.chain || !P.shifts_out) return;
+    // chain mode: the shift of exposure e is the sum of the pair shifts along its
+    // chain to ref (the level-0 shift rows hold the pairs' own shifts)
+    __syncthreads();
+    for (int e = threadIdx.x; e < L.n; e += kSearchThreads) {
+        int sx = 0, sy = 0;
+        for (int j = e; j != P.ref; j += e < P.ref ? 1 : -1) {
+            const int32_t *sj = Planes::shift(ws, L, j, 0);
+            sx += sj[0];
+            sy += sj[1];
+        }
+        P.shifts_out[2 * e] = sx;
+        P.shifts_out[2 * e + 1] = sy;
+    }
 }
 
 }  // namespace
