@@ -3,8 +3,9 @@
 
 A step is one pass of the whole path over one exposure stack: one
 mtb_align_stack_ex call, which enqueues the pyramid pass (k_clear, k_pyramid),
-the bitmap pass (k_bitmaps) and the coarse-to-fine shift search
-(k_clear_search, k_search), chained by programmatic dependent launch.  The
+the bitmap pass (k_bitmaps) and the coarse-to-fine shift search (k_search,
+which starts while the bitmaps are still being packed), chained by
+programmatic dependent launch.  The
 default workload is the 4000x3000 stack of 3 exposures (2 pairs, 7 levels).
 The metric is aligned MPix/s: full-resolution pixels of every aligned pair
 divided by the step time.  A second loop of the same length times the same work
@@ -20,9 +21,11 @@ with its data in HBM.  `e2e` times the host-buffer entry point
 out.  `cpu_baseline` times the single-threaded oracle on the same stack.
 
 Other workloads: `batchN` (N uneven stacks in one persistent launch, against the
-plain path) and `serve` (Poisson arrivals of 6000x4000x7 jobs into the serving
+plain path), `serve` (Poisson arrivals of 6000x4000x7 jobs into the serving
 loop under a 40 GB budget, swept over offered load; p50/p99 latency and served
-MPix/s per rate).
+MPix/s per rate), `apply` (moving the 6000x4000x7 exposures by their shifts)
+and `paper` (2560x1440 stacks of 2..7 exposures end to end, with the chain
+mode, the quadrant test and the shift application beside).
 
 Multi-GPU (torchrun): each rank aligns its own stack every step (weak scaling,
 no collective on the data path); the barrier and the max over ranks of the
@@ -57,8 +60,10 @@ FALLBACK_HBM_GBS = 6800.0
 # sources at capture time; reported only while the sources are unchanged.
 NCU_TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum (cold cache), one
-    # k_pyramid launch of the 4000x3000x3 stack: 109.84 MB read + 7.19 MB written
-    ("k_pyramid", "stack4000x3000x3"): {"bytes": 117027072, "sources_sha256": "9afd15a5479d5445de6b72220266167d3e1e1ced686e3de21639559134d3e338"},
+    # launch each: k_pyramid of the 4000x3000x3 stack (109.79 MB read + 7.58 MB
+    # written) and k_apply_shifts of the 6000x4000x7 stack (496.84 + 458.71 MB)
+    ("k_pyramid", "stack4000x3000x3"): {"bytes": 117372928, "sources_sha256": "891afa279cef59abd067b14fd03e3b67985905bf09398de1e39f1e0a8c16da26"},
+    ("k_apply_shifts", "apply6000x4000x7"): {"bytes": 955552256, "sources_sha256": "891afa279cef59abd067b14fd03e3b67985905bf09398de1e39f1e0a8c16da26"},
 }
 
 
@@ -75,7 +80,7 @@ def parse_args(argv=None):
     p.add_argument("--rates", default="10,30,100,300,1000,2000", help="serve: offered jobs/s")
     p.add_argument("--pool", type=int, default=32, help="serve: distinct pre-generated jobs")
     p.add_argument("--slots", type=int, default=8, help="serve: jobs on the GPU at most")
-    p.add_argument("--copy-streams", type=int, default=2, help="serve: copy streams per job")
+    p.add_argument("--copy-streams", type=int, default=1, help="serve: copy streams per job")
     p.add_argument("--budget-gb", type=float, default=40.0, help="serve: device-memory budget")
     return p.parse_args(argv)
 
@@ -139,7 +144,7 @@ def algorithmic_bytes(spec) -> dict:
 
 
 def kernels_per_step(spec) -> int:
-    return 5  # k_clear, k_pyramid, k_bitmaps, k_clear_search, k_search
+    return 4  # k_clear, k_pyramid, k_bitmaps, k_search
 
 
 def kernel_sources_digest() -> str:
@@ -152,8 +157,8 @@ def kernel_sources_digest() -> str:
     return h.hexdigest()
 
 
-def traffic_for(kernel: str, spec):
-    rec = NCU_TRAFFIC.get((kernel, spec.name))
+def traffic_for(kernel: str, workload: str):
+    rec = NCU_TRAFFIC.get((kernel, workload))
     if not rec:
         return None
     return rec["bytes"] if rec["sources_sha256"] == kernel_sources_digest() else None
@@ -337,7 +342,7 @@ def run_gb300(args):
     achieved = abytes["pyramid"] / (stage_ms["pyramid"] / 1e3) / 1e9
     roofline = {"bound": "hbm", "kernel": "k_pyramid", "achieved": round(achieved, 1), "peak": peak,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                "traffic": traffic_for("k_pyramid", spec), "algorithmic_bytes_per_launch": abytes["pyramid"],
+                "traffic": traffic_for("k_pyramid", spec.name), "algorithmic_bytes_per_launch": abytes["pyramid"],
                 "ms_per_launch": round(stage_ms["pyramid"], 5),
                 "share_of_staged_step": round(stage_ms["pyramid"] / staged_total, 3),
                 "duration_source": f"CUDA events around mtb_build_pyramids, {len(sev)} staged steps after the "
@@ -701,6 +706,142 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------- after the alignment
+def _time_calls(fn, K: int, W: int, stream, dev) -> float:
+    """Mean ms of fn() over K calls after W, CUDA events on the launching stream."""
+    import torch
+
+    for _ in range(max(3, W)):
+        fn()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(K):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    return e0.elapsed_time(e1) / K
+
+
+def run_apply(args):
+    """mtb_apply_shifts on the 6000x4000x7 stack with its own shifts: every
+    exposure moved (edge fill), 3 bytes read and 3 written per pixel."""
+    import torch
+
+    from paper_2007_06483_gb300 import build as cuda_build
+
+    cuda_build.build()
+    import paper_2007_06483_gb300 as mtb
+    from paper_2007_06483_gb300 import synth
+
+    spec = synth.STACK_24MP
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream(dev)
+    imgs = synth.make_stack(spec, dev)
+    shifts = mtb.align_stack(imgs, spec.levels, spec.noise_tol, spec.ref, stream=stream)
+    outs = [torch.empty_like(imgs) for _ in range(2)]  # 2 x 504 MB: each step misses L2
+    k = [0]
+
+    def step():
+        mtb.apply_shifts(imgs, shifts, mtb.MTB_FILL_EDGE, out=outs[k[0] % 2], stream=stream)
+        k[0] += 1
+
+    sampler = ClockSampler(dev.index or 0)
+    sampler.start()
+    ms = _time_calls(step, args.steps, args.warmup, stream, dev)
+    clocks = sampler.stop()
+    px = spec.n * spec.w * spec.h
+    moved = 2 * spec.input_bytes
+    peak, peak_kind = hbm_peak()
+    achieved = moved / (ms / 1e3) / 1e9
+    line = {
+        "metric": "moved MPix/s (all exposures, RGB)", "value": round(px / (ms / 1e3) / 1e6, 1), "unit": "MPix/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 5),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": "apply6000x4000x7", "fill": "edge", "l2": "504 MB in, 2 x 504 MB out (> L2)"},
+        "roofline": {"bound": "hbm", "kernel": "k_apply_shifts", "achieved": round(achieved, 1), "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "traffic": traffic_for("k_apply_shifts", "apply6000x4000x7"),
+                     "algorithmic_bytes_per_launch": moved},
+        "gpu_launches": args.steps, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_paper(args):
+    """The paper's measurement shape (Sec. IV): 2560x1440 stacks of 2..7
+    exposures, timed end to end from pinned host memory (copy in, align, shifts
+    out), as the paper includes the CPU-to-GPU transfer, and with the inputs
+    already on the device; the chain mode, the quadrant test and moving the
+    exposures are timed beside.  The oracle on one host core gives the context
+    the paper's CPU column gives."""
+    import numpy as np
+    import torch
+
+    from paper_2007_06483_gb300 import build as cuda_build
+
+    cuda_build.build()
+    import paper_2007_06483_gb300 as mtb
+    from paper_2007_06483_gb300 import synth
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream(dev)
+    K, W = args.steps, args.warmup
+    rows = []
+    for spec in synth.paper_specs():
+        n, w, h, L = spec.n, spec.w, spec.h, spec.levels
+        imgs = synth.make_stack(spec, dev)
+        host = imgs.cpu().pin_memory()
+        ws = mtb.new_workspace(n, w, h, L, device=dev)
+        dws = torch.empty(mtb.host_workspace_bytes(n, w, h, L), dtype=torch.uint8, device=dev)
+        qws = torch.empty(mtb.lib().mtb_quadrant_workspace_bytes(n, w, h, L - 1), dtype=torch.uint8, device=dev)
+        out = torch.empty((n, 2), dtype=torch.int32, device=dev)
+        moved = torch.empty_like(imgs)
+        t = {}
+        t["e2e_ms"] = _time_calls(lambda: mtb.align_stack_host(host, L, spec.noise_tol, spec.ref,
+                                                               device_workspace=dws, stream=stream), K, W, stream, dev)
+        t["device_ms"] = _time_calls(lambda: mtb.align_stack(imgs, L, spec.noise_tol, spec.ref, workspace=ws, out=out,
+                                                             stream=stream), K, W, stream, dev)
+        t["chain_ms"] = _time_calls(lambda: mtb.align_stack_chain(imgs, L, spec.noise_tol, spec.ref, workspace=ws,
+                                                                  out=out, stream=stream), K, W, stream, dev)
+        t["quadrants_ms"] = _time_calls(lambda: mtb.align_quadrants(imgs, L - 1, spec.noise_tol, spec.ref, 1,
+                                                                    workspace=qws, stream=stream), K, W, stream, dev)
+        t["apply_ms"] = _time_calls(lambda: mtb.apply_shifts(imgs, out, mtb.MTB_FILL_EDGE, out=moved, stream=stream),
+                                    K, W, stream, dev)
+        shifts = mtb.align_stack(imgs, L, spec.noise_tol, spec.ref, stream=stream).cpu().numpy()
+        row = {"n": n, **{k: round(v, 4) for k, v in t.items()},
+               "e2e_mpix_s": round(spec.aligned_pixels / (t["e2e_ms"] / 1e3) / 1e6, 1),
+               "device_mpix_s": round(spec.aligned_pixels / (t["device_ms"] / 1e3) / 1e6, 1),
+               "planted_recovered": bool(np.array_equal(shifts, synth.expected_shifts(spec)))}
+        if not args.no_cpu_baseline:
+            import oracle
+
+            t0 = time.perf_counter()
+            res = oracle.align_stack(host.numpy(), L, spec.noise_tol, spec.ref)
+            cpu_ms = (time.perf_counter() - t0) * 1e3
+            row["oracle_1core_ms"] = round(cpu_ms, 1)
+            row["e2e_speedup_vs_oracle"] = round(cpu_ms / t["e2e_ms"], 1)
+            row["gpu_equals_oracle"] = bool(np.array_equal(shifts, res["shifts"]))
+        rows.append(row)
+        del imgs, host, ws, dws, qws, moved
+    last = rows[-1]
+    line = {
+        "metric": METRIC + " (end to end, paper shape)", "value": last["e2e_mpix_s"], "unit": UNIT, "n_gpus": 1,
+        "steps": K, "warmup": W, "ms_per_step": last["e2e_ms"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": "paper2560x1440x2..7", "levels": 6, "quadrant_levels": 5,
+                   "e2e": "pinned host -> device copy, alignment, shifts -> host"},
+        "per_n": rows,
+        "e2e": {"value": last["e2e_mpix_s"], "unit": UNIT, "h2d_bytes_per_step": 7 * 2560 * 1440 * 3,
+                "d2h_bytes_per_step": 7 * 8},
+        "cpu_baseline": None if args.no_cpu_baseline else {
+            "value": round(synth.paper_specs()[-1].aligned_pixels / (last["oracle_1core_ms"] / 1e3) / 1e6, 2),
+            "unit": UNIT, "cores": 1, "kind": "oracle", "sample": "one run per stack size, single-threaded C oracle"},
+        "gpu_launches": kernels_per_step(None) * K,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
@@ -709,6 +850,10 @@ def main(argv=None):
         run_batch(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "apply":
+        run_apply(args)
+    elif args.workload == "paper":
+        run_paper(args)
     else:
         run_gb300(args)
 

@@ -56,6 +56,29 @@ __device__ __forceinline__ uint8_t apply_byte(const uint8_t *__restrict__ in, co
     return in[(long long)e * exp_bytes + ys * row_bytes + xs * 3 + ch];
 }
 
+// A chunk outside the row's interior: all fill (a zero-filled row), or byte by
+// byte (the row ends, a chunk shared with the next row, the stack's last bytes).
+__device__ __forceinline__ void edge_chunk(const uint8_t *__restrict__ in, const int32_t *__restrict__ shifts, int w,
+                                           int h, int fill, uint8_t *__restrict__ out, long long k, long long r0,
+                                           long long row_bytes, long long total, bool zero_row) {
+    const long long g = k << 4;
+    const long long c = g - r0;
+    uint4 v;
+    if (c + 16 <= row_bytes && zero_row) {
+        v = make_uint4(0u, 0u, 0u, 0u);
+    } else {
+        uint32_t b[4] = {0u, 0u, 0u, 0u};
+        for (int j = 0; j < 16 && g + j < total; ++j)
+            b[j >> 2] |= (uint32_t)apply_byte(in, shifts, g + j, w, h, fill) << (8 * (j & 3));
+        if (g + 16 > total) {  // the stack's last bytes: no store past its end
+            for (int j = 0; g + j < total; ++j) out[g + j] = (uint8_t)(b[j >> 2] >> (8 * (j & 3)));
+            return;
+        }
+        v = make_uint4(b[0], b[1], b[2], b[3]);
+    }
+    __stcs(reinterpret_cast<uint4 *>(out + g), v);
+}
+
 // Warp v of the grid takes output rows v, v + (warps in the grid), ... of the
 // n*h rows; a row owns the 16-byte chunks whose first byte lies in it, and the
 // lanes take its chunks in turn (coalesced 512-byte steps).
@@ -84,29 +107,48 @@ k_apply_shifts(const uint8_t *__restrict__ in, int n, int w, int h, const int32_
         const long long src0 = ((long long)e * h + ys) * row_bytes - sxb;
         const int r = (int)((((src0 - r0) % 16) + 16) % 16);
         const bool zero_row = !row_in && fill == 0;
-        for (long long k = k_first + lane; k <= k_last; k += 32) {
-            const long long g = k << 4;
-            const long long c = g - r0;
-            uint4 v;
-            if (c + 16 <= row_bytes && zero_row) {
-                v = make_uint4(0u, 0u, 0u, 0u);
-            } else if (c + 16 <= row_bytes && c >= c_lo && c + 16 <= c_hi) {
-                const long long s = src0 + c;  // 16 source bytes [s, s + 16) inside the source row
+        // chunks whose 16 bytes all come from inside the source row: a
+        // branch-free loop with 4 chunks (8 loads) in flight per lane
+        long long k_in_lo = k_last + 1, k_in_hi = k_last;  // empty unless set below
+        if (!zero_row) {
+            const long long c_end = (c_hi < row_bytes ? c_hi : row_bytes) - 16;
+            if (c_end >= c_lo) {
+                k_in_lo = (r0 + c_lo + 15) >> 4;
+                k_in_hi = (r0 + c_end) >> 4;
+                if (k_in_lo < k_first) k_in_lo = k_first;
+                if (k_in_hi > k_last) k_in_hi = k_last;
+                if (k_in_hi < k_in_lo) k_in_lo = k_last + 1, k_in_hi = k_last;
+            }
+        }
+        if (k_in_lo <= k_in_hi) {
+            long long k = k_in_lo + lane;
+            for (; k + 96 <= k_in_hi; k += 128) {
+                uint4 a[4], b[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const long long s = src0 + ((k + 32 * u) << 4) - r0;
+                    const uint4 *p = reinterpret_cast<const uint4 *>(in + (s - r));
+                    a[u] = __ldcs(p);
+                    b[u] = r == 0 ? a[u] : __ldcs(p + 1);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    __stcs(reinterpret_cast<uint4 *>(out + ((k + 32 * u) << 4)), r == 0 ? a[u] : window16(a[u], b[u], r));
+            }
+            for (; k <= k_in_hi; k += 32) {
+                const long long s = src0 + (k << 4) - r0;
                 const uint4 *p = reinterpret_cast<const uint4 *>(in + (s - r));
                 const uint4 a = __ldcs(p);
-                v = r == 0 ? a : window16(a, __ldcs(p + 1), r);  // the second block holds byte s + 15
-            } else {
-                uint32_t b[4] = {0u, 0u, 0u, 0u};
-                for (int j = 0; j < 16 && g + j < total; ++j)
-                    b[j >> 2] |= (uint32_t)apply_byte(in, shifts, g + j, w, h, fill) << (8 * (j & 3));
-                if (g + 16 > total) {  // the stack's last bytes: no store past its end
-                    for (int j = 0; g + j < total; ++j) out[g + j] = (uint8_t)(b[j >> 2] >> (8 * (j & 3)));
-                    continue;
-                }
-                v = make_uint4(b[0], b[1], b[2], b[3]);
+                __stcs(reinterpret_cast<uint4 *>(out + (k << 4)), r == 0 ? a : window16(a, __ldcs(p + 1), r));
             }
-            __stcs(reinterpret_cast<uint4 *>(out + g), v);
         }
+        // the other chunks (fill, the row ends, chunks shared with the next row):
+        // before and after the interior range
+        const long long k_mid = k_in_lo < k_last + 1 ? k_in_lo : k_last + 1;
+        for (long long k = k_first + lane; k < k_mid; k += 32) edge_chunk(in, shifts, w, h, fill, out, k, r0, row_bytes,
+                                                                        total, zero_row);
+        for (long long k = (k_in_hi + 1 > k_first ? k_in_hi + 1 : k_first) + lane; k <= k_last; k += 32)
+            edge_chunk(in, shifts, w, h, fill, out, k, r0, row_bytes, total, zero_row);
     }
 }
 

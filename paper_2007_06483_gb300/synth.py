@@ -208,6 +208,18 @@ def serve_specs(count: int = 32) -> List[StackSpec]:
             for k in range(count)]
 
 
+def paper_specs() -> List[StackSpec]:
+    """The paper's measurement shape (Sec. IV): 2560x1440 (3.7 MP) exposures,
+    stacks of 2 to 7, 6 pyramid levels; gains 2^(k - n//2) with gamma 2.2 and
+    N(0, 1) sensor noise, handheld-size displacements within +-24 px, ref the
+    middle exposure."""
+    out = []
+    for n in range(2, 8):
+        gains = tuple(2.0 ** (k - n // 2) for k in range(n))
+        out.append(StackSpec(f"paper2560x1440x{n}", 7000 + n, 2560, 1440, n, gains, 2.2, 1.0, 24, 6, 4, n // 2))
+    return out
+
+
 def small_spec(seed: int, w: int, h: int, n: int = 2, levels: int = 3, shift_range: int = 5,
                noise_tol: int = 4, ref: int = 0, gamma: Optional[float] = 2.2) -> StackSpec:
     """Small stacks for tests: gains 2^(k - ref)."""
