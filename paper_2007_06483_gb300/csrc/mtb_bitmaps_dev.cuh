@@ -128,26 +128,48 @@ __device__ __forceinline__ void bitmap_chunk_of(const mtb_layout_t &L, int item,
 // median from the pyramid pass, pack, and count the chunk as done.
 __device__ void bitmap_chunk(const mtb_layout_t &L, uint8_t *ws, int tol, int e, int l, int c, int chunk_words,
                              int *s_med) {
+    constexpr int kGroup = 4;  // words whose gray loads a thread issues together
+    const int Wl = L.width[l], Hl = L.height[l], bp = L.bits_pitch[l], gpl = L.gray_pitch[l];
+    const uint8_t *__restrict__ g = Planes::gray(ws, L, e, l);
+    uint2 *__restrict__ out = Planes::bits(ws, L, e, l);
+    const int words = bp * Hl;
+    const int w_end = min(words, (c + 1) * chunk_words);
+    uint4 va[kGroup], vb[kGroup];
+    // the gray loads of a group are issued before any store (and the first
+    // group's before the median is read), so they are all in flight together
+    auto load_group = [&](int i0) {
+#pragma unroll
+        for (int j = 0; j < kGroup; ++j) {
+            const int idx = i0 + j * (int)blockDim.x;
+            va[j] = vb[j] = make_uint4(0u, 0u, 0u, 0u);
+            if (idx < w_end) {
+                const int y = idx / bp, x = (idx - y * bp) * 32;
+                if (x < Wl) {
+                    const uint4 *p = reinterpret_cast<const uint4 *>(g + (size_t)y * gpl + x);
+                    va[j] = __ldcs(p);
+                    vb[j] = __ldcs(p + 1);
+                }
+            }
+        }
+    };
+    int i0 = c * chunk_words + (int)threadIdx.x;
+    load_group(i0);
     if (threadIdx.x == 0) *s_med = *Planes::median(ws, L, e, l);
     __syncthreads();
     const Thresholds th(*s_med, tol);
-    const int Wl = L.width[l], Hl = L.height[l], bp = L.bits_pitch[l], gpl = L.gray_pitch[l];
-    const uint8_t *g = Planes::gray(ws, L, e, l);
-    uint2 *out = Planes::bits(ws, L, e, l);
-    const int words = bp * Hl;
-    const int w_end = min(words, (c + 1) * chunk_words);
-#pragma unroll 4
-    for (int idx = c * chunk_words + threadIdx.x; idx < w_end; idx += blockDim.x) {
-        const int y = idx / bp, q = idx - y * bp;
-        const int x = q * 32;
-        uint2 r = make_uint2(0u, 0u);
-        if (x < Wl) {
-            const uint4 *p = reinterpret_cast<const uint4 *>(g + (size_t)y * gpl + x);
-            const uint4 a = __ldcs(p), b = __ldcs(p + 1);
-            const uint32_t v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-            r = pack_bits(v, th, min(32, Wl - x));
+    for (;;) {
+#pragma unroll
+        for (int j = 0; j < kGroup; ++j) {
+            const int idx = i0 + j * (int)blockDim.x;
+            if (idx < w_end) {
+                const int y = idx / bp, x = (idx - y * bp) * 32;
+                const uint32_t v[8] = {va[j].x, va[j].y, va[j].z, va[j].w, vb[j].x, vb[j].y, vb[j].z, vb[j].w};
+                out[idx] = x < Wl ? pack_bits(v, th, min(32, Wl - x)) : make_uint2(0u, 0u);
+            }
         }
-        out[idx] = r;
+        i0 += kGroup * (int)blockDim.x;
+        if (i0 >= w_end) break;
+        load_group(i0);
     }
     cta_signal(Ctr::bit_done(ws, L, e, l));
 }
