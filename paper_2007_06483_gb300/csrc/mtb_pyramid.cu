@@ -23,8 +23,10 @@
 namespace mtb {
 namespace {
 
+// kAligned (W a multiple of 16): the RGB of tile t+1 is loaded into registers
+// while the CTA builds levels 1..5 of tile t (3 CTAs per SM leave room for it).
 template <bool kAligned>
-__global__ void __launch_bounds__(kPyrThreads, 4)
+__global__ void __launch_bounds__(kPyrThreads, kAligned ? 3 : 4)
 k_pyramid(const uint8_t *__restrict__ images, const mtb_layout_t L, uint8_t *__restrict__ ws, int tiles_x,
           int tiles_per_exp, int total_tiles) {
     static_assert(kPyrThreads == 256, "one thread per histogram bin in the flush");
@@ -38,10 +40,24 @@ k_pyramid(const uint8_t *__restrict__ images, const mtb_layout_t L, uint8_t *__r
     pdl_trigger();
     const int t0 = (int)(((long long)blockIdx.x * total_tiles) / gridDim.x);
     const int t1 = (int)(((long long)(blockIdx.x + 1) * total_tiles) / gridDim.x);
+    auto origin = [&](int t, int *e, int *y0, int *x0) {
+        *e = t / tiles_per_exp;
+        const int rt = t - *e * tiles_per_exp;
+        const int ty = rt / tiles_x;
+        *y0 = ty * kTileRows;
+        *x0 = (rt - ty * tiles_x) * kTileCols;
+    };
+    TileRgb cur, nxt;
+    if (kAligned && t0 < t1) {
+        int e, y0, x0;
+        origin(t0, &e, &y0, &x0);
+        tile_load_rgb(images, L, e, y0, x0, min(kTileRows, L.h - y0), min(kTileCols, L.w - x0), cur);
+    }
     int cur_e = -1, done = 0;
     bool waited = false;
     for (int t = t0; t < t1; ++t) {
-        const int e = t / tiles_per_exp;
+        int e, y0, x0;
+        origin(t, &e, &y0, &x0);
         if (e != cur_e) {
             if (cur_e >= 0) {
                 if (!waited) pdl_wait();  // the histograms were cleared by the previous kernel
@@ -51,16 +67,18 @@ k_pyramid(const uint8_t *__restrict__ images, const mtb_layout_t L, uint8_t *__r
             cur_e = e;
             done = 0;
         }
-        const int rt = t - e * tiles_per_exp;
-        const int ty = rt / tiles_x;
-        const int tx = rt - ty * tiles_x;
-        const int y0 = ty * kTileRows, x0 = tx * kTileCols;
         const int rows = min(kTileRows, L.h - y0);
         const int cols = min(kTileCols, L.w - x0);
-        if (kAligned)
-            tile_level0_aligned(images, L, ws, e, y0, x0, rows, cols, sm);
-        else
+        if (kAligned) {
+            tile_level0_loaded(cur, L, ws, e, y0, x0, rows, cols, sm);
+            if (t + 1 < t1) {  // in flight while levels 1..5 of this tile are built
+                int e1, y1, x1;
+                origin(t + 1, &e1, &y1, &x1);
+                tile_load_rgb(images, L, e1, y1, x1, min(kTileRows, L.h - y1), min(kTileCols, L.w - x1), nxt);
+            }
+        } else {
             tile_level0_general(images, L, ws, e, y0, x0, rows, cols, sm);
+        }
         __syncthreads();
         if (!kAligned) tile_store_level0(L, ws, e, y0, x0, rows, cols, sm);
         if (K >= 1) tile_levels12(L, ws, e, y0, x0, K, sm);
@@ -69,6 +87,7 @@ k_pyramid(const uint8_t *__restrict__ images, const mtb_layout_t L, uint8_t *__r
         // writes level 0 of the shared buffer
         if (K >= 3) tile_block_tail(L, ws, e, y0, x0, K, sm);
         ++done;
+        if (kAligned) cur = nxt;
     }
     if (cur_e >= 0) {
         if (!waited) pdl_wait();

@@ -112,6 +112,47 @@ __device__ __forceinline__ void tile_level0_aligned(const uint8_t *__restrict__ 
     }
 }
 
+// The same, split in two: the RGB of a tile loaded into registers (issued one
+// tile ahead), then level 0 made from them.
+struct TileRgb {
+    uint4 raw[kTileRows * (kTileCols / 16) / kPyrThreads][3];
+};
+__device__ __forceinline__ void tile_load_rgb(const uint8_t *__restrict__ images, const mtb_layout_t &L, int e,
+                                              int y0, int x0, int rows, int cols, TileRgb &t) {
+    const int tid = threadIdx.x;
+    const uint64_t W = (uint64_t)L.w;
+    const uint64_t e0 = (uint64_t)e * W * (uint64_t)L.h;
+#pragma unroll
+    for (int k = 0; k < kTileRows * (kTileCols / 16) / kPyrThreads; ++k) {
+        const int grp = tid + k * kPyrThreads;
+        const int r = grp >> 4, c = (grp & 15) << 4;
+        if (r < rows && c < cols) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(images + 3 * (e0 + (uint64_t)(y0 + r) * W + x0 + c));
+            t.raw[k][0] = __ldcs(src);
+            t.raw[k][1] = __ldcs(src + 1);
+            t.raw[k][2] = __ldcs(src + 2);
+        }
+    }
+}
+__device__ __forceinline__ void tile_level0_loaded(const TileRgb &t, const mtb_layout_t &L, uint8_t *ws, int e,
+                                                   int y0, int x0, int rows, int cols, PyrShared &sm) {
+    const int tid = threadIdx.x;
+    uint8_t *g0 = Planes::gray(ws, L, e, 0);
+    const size_t gp0 = (size_t)L.gray_pitch[0];
+    uint32_t *h0 = sm.h01[0][tid >> 5];
+#pragma unroll
+    for (int k = 0; k < kTileRows * (kTileCols / 16) / kPyrThreads; ++k) {
+        const int grp = tid + k * kPyrThreads;
+        const int r = grp >> 4, c = (grp & 15) << 4;
+        if (r >= rows || c >= cols) continue;
+        uint32_t g[16];
+        const uint4 v = gray16(t.raw[k][0], t.raw[k][1], t.raw[k][2], g);
+        *reinterpret_cast<uint4 *>(sm.lv + r * kTileCols + c) = v;
+        *reinterpret_cast<uint4 *>(g0 + (size_t)(y0 + r) * gp0 + x0 + c) = v;
+        hist_group(h0, g, v, 0, 16);
+    }
+}
+
 // Any W: the tile row's pixels are a flat run [p0, p0 + cols) that starts
 // anywhere inside a 16-pixel group, so groups are clipped to it.
 __device__ __forceinline__ void tile_level0_general(const uint8_t *__restrict__ images, const mtb_layout_t &L,
