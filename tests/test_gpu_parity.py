@@ -109,7 +109,8 @@ def test_one_call_matches_stages(mtb_lib, oracle_mod):
     imgs = synth.make_stack(spec, "cuda")
     shifts, errs, lsh = mtb_lib.align_stack(imgs, spec.levels, 4, spec.ref, level_outputs=True)
     plain = mtb_lib.align_stack(imgs, spec.levels, 4, spec.ref)
-    host = mtb_lib.align_stack_host(imgs.cpu().pin_memory(), spec.levels, 4, spec.ref)
+    host = mtb_lib.align_stack_host(imgs.cpu().pin_memory(), spec.levels, 4, spec.ref)  # read in place
+    paged = mtb_lib.align_stack_host(imgs.cpu().contiguous(), spec.levels, 4, spec.ref)  # copied first
     torch.cuda.synchronize()
     want = oracle_mod.align_stack(imgs.cpu().numpy(), spec.levels, 4, spec.ref)
     assert np.array_equal(errs.cpu().numpy().view(np.uint32), want["level_errs"])
@@ -117,6 +118,7 @@ def test_one_call_matches_stages(mtb_lib, oracle_mod):
     assert np.array_equal(shifts.cpu().numpy(), want["shifts"])
     assert np.array_equal(plain.cpu().numpy(), want["shifts"])
     assert np.array_equal(host.numpy(), want["shifts"])
+    assert np.array_equal(paged.numpy(), want["shifts"])
 
 
 def test_repeatable(mtb_lib):
