@@ -56,14 +56,14 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
-# ncu capture, keyed by kernel and workload, with the SHA-256 of the CUDA
-# sources at capture time; reported only while the sources are unchanged.
+# ncu capture, keyed by kernel and workload, with the SHA-256 of that kernel's
+# sources at capture time; reported only while those sources are unchanged.
 NCU_TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum (cold cache), one
-    # launch each: k_pyramid of the 4000x3000x3 stack (109.79 MB read + 7.58 MB
+    # launch each: k_pyramid of the 4000x3000x3 stack (109.71 MB read + 7.29 MB
     # written) and k_apply_shifts of the 6000x4000x7 stack (496.84 + 458.71 MB)
-    ("k_pyramid", "stack4000x3000x3"): {"bytes": 117372928, "sources_sha256": "891afa279cef59abd067b14fd03e3b67985905bf09398de1e39f1e0a8c16da26"},
-    ("k_apply_shifts", "apply6000x4000x7"): {"bytes": 955552256, "sources_sha256": "891afa279cef59abd067b14fd03e3b67985905bf09398de1e39f1e0a8c16da26"},
+    ("k_pyramid", "stack4000x3000x3"): {"bytes": 117000960, "sources_sha256": "34a0587c98bb6776ad50c83391b1116f97192890e415866210c8eeb8a4b3e506"},
+    ("k_apply_shifts", "apply6000x4000x7"): {"bytes": 955552256, "sources_sha256": "40536e741a1378bde169320db4c200f28e2922bc0e77e2b9c23f2d8cca0bbc17"},
 }
 
 
@@ -147,13 +147,20 @@ def kernels_per_step(spec) -> int:
     return 4  # k_clear, k_pyramid, k_bitmaps, k_search
 
 
-def kernel_sources_digest() -> str:
-    """SHA-256 over the library's CUDA sources (any change voids a stored ncu figure)."""
+KERNEL_SOURCES = {  # the files each recorded kernel is built from
+    "k_pyramid": ("mtb_pyramid.cu", "mtb_pyramid_dev.cuh", "mtb_device.cuh", "mtb_internal.cuh"),
+    "k_apply_shifts": ("mtb_apply.cu", "mtb_internal.cuh"),
+}
+
+
+def kernel_sources_digest(kernel: str) -> str:
+    """SHA-256 over the CUDA sources a kernel is built from (and the C ABI
+    header); any change voids a stored ncu figure."""
     csrc = os.path.join(ROOT, "paper_2007_06483_gb300", "csrc")
     h = hashlib.sha256()
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in KERNEL_SOURCES[kernel]:
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    h.update(open(os.path.join(ROOT, "include", "mtb.h"), "rb").read())
     return h.hexdigest()
 
 
@@ -161,7 +168,7 @@ def traffic_for(kernel: str, workload: str):
     rec = NCU_TRAFFIC.get((kernel, workload))
     if not rec:
         return None
-    return rec["bytes"] if rec["sources_sha256"] == kernel_sources_digest() else None
+    return rec["bytes"] if rec["sources_sha256"] == kernel_sources_digest(kernel) else None
 
 
 def hbm_peak():
