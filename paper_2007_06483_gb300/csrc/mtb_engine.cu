@@ -78,6 +78,7 @@ struct EngineShared {
     PyrShared pyr;
     SearchShared search;
     uint32_t hist[256];
+    mtb_layout_t L;  // the layout of the stack a pyramid item works on
     int med;
     int stack, phase, local, ok;
 };
@@ -88,27 +89,44 @@ __device__ __forceinline__ int pyr_exposure(const StackDesc &d, int j) {
     return j == 0 ? d.sp.ref : (j <= d.sp.ref ? j - 1 : j);
 }
 
+static_assert(sizeof(mtb_layout_t) % 4 == 0, "the layout is copied to shared memory as 32-bit words");
+
 __device__ __noinline__ void pyr_item(const StackDesc &d, int k, EngineShared &sm) {
-    const mtb_layout_t &L = d.L;
+    // the stack's layout in shared memory: the tile functions read its fields
+    // for every tile and level
+    {
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(&d.L);
+        uint32_t *dst = reinterpret_cast<uint32_t *>(&sm.L);
+        for (int v = threadIdx.x; v < (int)(sizeof(mtb_layout_t) / 4); v += kEngineThreads) dst[v] = src[v];
+        __syncthreads();
+    }
+    const mtb_layout_t &L = sm.L;
     const int e = pyr_exposure(d, k / d.pyr_items);
     const int t0 = (k % d.pyr_items) * d.pyr_chunk;
     const int t1 = min(d.tiles_per_exp, t0 + d.pyr_chunk);
     const int K = L.tile_levels - 1;
+    const int tiles_x = d.tiles_x, aligned = d.aligned;
+    const uint8_t *images = d.images;
+    uint8_t *ws = d.ws;
+    int ty = t0 / tiles_x, tx = t0 - ty * tiles_x;
     for (int t = t0; t < t1; ++t) {
-        const int ty = t / d.tiles_x, tx = t - ty * d.tiles_x;
         const int y0 = ty * kTileRows, x0 = tx * kTileCols;
         const int rows = min(kTileRows, L.h - y0), cols = min(kTileCols, L.w - x0);
-        if (d.aligned)
-            tile_level0_aligned(d.images, L, d.ws, e, y0, x0, rows, cols, sm.pyr);
+        if (++tx == tiles_x) {
+            tx = 0;
+            ++ty;
+        }
+        if (aligned)
+            tile_level0_aligned(images, L, ws, e, y0, x0, rows, cols, sm.pyr);
         else
-            tile_level0_general(d.images, L, d.ws, e, y0, x0, rows, cols, sm.pyr);
+            tile_level0_general(images, L, ws, e, y0, x0, rows, cols, sm.pyr);
         __syncthreads();
-        if (!d.aligned) tile_store_level0(L, d.ws, e, y0, x0, rows, cols, sm.pyr);
-        if (K >= 1) tile_levels12(L, d.ws, e, y0, x0, K, sm.pyr);
+        if (!aligned) tile_store_level0(L, ws, e, y0, x0, rows, cols, sm.pyr);
+        if (K >= 1) tile_levels12(L, ws, e, y0, x0, K, sm.pyr);
         __syncthreads();
-        if (K >= 3) tile_block_tail(L, d.ws, e, y0, x0, K, sm.pyr);
+        if (K >= 3) tile_block_tail(L, ws, e, y0, x0, K, sm.pyr);
     }
-    flush_exposure(L, d.ws, e, t1 - t0, d.tiles_per_exp, K, sm.pyr);
+    flush_exposure(L, ws, e, t1 - t0, d.tiles_per_exp, K, sm.pyr);
 }
 
 // Waits (thread 0) for exposure e's pyramid pass; false if the wait gave up.
