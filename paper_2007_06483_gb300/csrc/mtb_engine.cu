@@ -109,22 +109,46 @@ __device__ __noinline__ void pyr_item(const StackDesc &d, int k, EngineShared &s
     const uint8_t *images = d.images;
     uint8_t *ws = d.ws;
     int ty = t0 / tiles_x, tx = t0 - ty * tiles_x;
-    for (int t = t0; t < t1; ++t) {
-        const int y0 = ty * kTileRows, x0 = tx * kTileCols;
-        const int rows = min(kTileRows, L.h - y0), cols = min(kTileCols, L.w - x0);
-        if (++tx == tiles_x) {
-            tx = 0;
-            ++ty;
+    if (aligned) {
+        // levels 0..2 from registers, one barrier, levels 3..5 by the half of
+        // the warps that alternates with the tile (the stage kernel's path
+        // without its prefetch: the engine runs at 4 CTAs per SM)
+        uint8_t *ebase = ws + (size_t)e * L.gray_exposure_stride;
+        for (int t = t0; t < t1; ++t) {
+            const int y0 = ty * kTileRows, x0 = tx * kTileCols;
+            const int rows = min(kTileRows, L.h - y0), cols = min(kTileCols, L.w - x0);
+            if (++tx == tiles_x) {
+                tx = 0;
+                ++ty;
+            }
+            const bool full = rows == kTileRows && cols == kTileCols;
+            uint8_t *lv2 = sm.pyr.lv + ((t - t0) & 1) * kLv2Bytes;
+            TileRgb rgb;
+            tile_load_rgb(images, L, e, y0, x0, rows, cols, rgb);
+            if (full) tile_levels012<true>(rgb, L, ebase, y0, x0, rows, cols, K, sm.pyr, lv2);
+            else tile_levels012<false>(rgb, L, ebase, y0, x0, rows, cols, K, sm.pyr, lv2);
+            __syncthreads();
+            const int a = (threadIdx.x >> 5) - (((t - t0) & 1) ? 4 : 0);
+            if (K >= 3 && a >= 0 && a < 4) {
+                if (full) tile_tail<true>(L, ebase, y0, x0, K, sm.pyr, lv2, a);
+                else tile_tail<false>(L, ebase, y0, x0, K, sm.pyr, lv2, a);
+            }
         }
-        if (aligned)
-            tile_level0_aligned(images, L, ws, e, y0, x0, rows, cols, sm.pyr);
-        else
+    } else {
+        for (int t = t0; t < t1; ++t) {
+            const int y0 = ty * kTileRows, x0 = tx * kTileCols;
+            const int rows = min(kTileRows, L.h - y0), cols = min(kTileCols, L.w - x0);
+            if (++tx == tiles_x) {
+                tx = 0;
+                ++ty;
+            }
             tile_level0_general(images, L, ws, e, y0, x0, rows, cols, sm.pyr);
-        __syncthreads();
-        if (!aligned) tile_store_level0(L, ws, e, y0, x0, rows, cols, sm.pyr);
-        if (K >= 1) tile_levels12(L, ws, e, y0, x0, K, sm.pyr);
-        __syncthreads();
-        if (K >= 3) tile_block_tail(L, ws, e, y0, x0, K, sm.pyr);
+            __syncthreads();
+            tile_store_level0(L, ws, e, y0, x0, rows, cols, sm.pyr);
+            if (K >= 1) tile_levels12(L, ws, e, y0, x0, K, sm.pyr);
+            __syncthreads();
+            if (K >= 3) tile_block_tail(L, ws, e, y0, x0, K, sm.pyr);
+        }
     }
     flush_exposure(L, ws, e, t1 - t0, d.tiles_per_exp, K, sm.pyr);
 }

@@ -8,56 +8,44 @@
 //     Sec. III-B).
 // A CTA owns 32-row x 256-column tiles of full-resolution pixels.  Level-l
 // pixels of a tile have their whole 2^l x 2^l source block inside it (l <= 5),
-// so the tile's part of levels 1..5 is built in shared memory from the gray
-// tile.  HBM traffic per full-resolution pixel: 3 bytes read (RGB) + 4/3 bytes
-// written (gray levels).
+// so the tile's part of levels 1..5 is built on chip from the gray tile.  HBM
+// traffic per full-resolution pixel: 3 bytes read (RGB) + 4/3 bytes written
+// (gray levels).
 //
 // Instruction budget: at HBM speed the pass has about 17 thread-instructions per
 // pixel, so the gray conversion uses two two-way dot products per pixel on the
 // RGB words as loaded, gray is packed with byte permutes, the 2x2 shrink is
-// done on 16-bit lanes, and a 16-pixel group of one value adds to the histogram
-// with a single shared atomic (saturated regions would otherwise serialise 32
-// lanes on one bin).
+// done on 16-bit lanes, histogram counts are shared-memory reductions on
+// 32-bit shared addresses, and (widths a multiple of 16) levels 1..5 come from
+// registers and warp shuffles rather than shared-memory round trips.
 #include "mtb_pyramid_dev.cuh"
 
 namespace mtb {
 namespace {
 
-// kAligned (W a multiple of 16): the RGB of tile t+1 is loaded into registers
-// while the CTA builds levels 1..5 of tile t (3 CTAs per SM leave room for it).
-template <bool kAligned>
-__global__ void __launch_bounds__(kPyrThreads, kAligned ? 3 : 4)
-k_pyramid(const uint8_t *__restrict__ images, const mtb_layout_t L, uint8_t *__restrict__ ws, int tiles_x,
-          int tiles_per_exp, int total_tiles) {
-    static_assert(kPyrThreads == 256, "one thread per histogram bin in the flush");
-    __shared__ PyrShared sm;
-    const int tid = threadIdx.x;
+// Widths that are a multiple of 16.  The next tile's RGB is loaded into
+// registers (3 CTAs per SM leave room for it) while levels 0..2 of the current
+// one are built; after the tile's one barrier, levels 3..5 are built by half of
+// the warps (alternating with the tile, from one of two level-2 buffers) while
+// the others go on.
+__device__ __forceinline__ void pyramid_aligned(const uint8_t *__restrict__ images, const mtb_layout_t &L,
+                                                uint8_t *__restrict__ ws, int tiles_x, int tiles_per_exp, int t0,
+                                                int t1, PyrShared &sm) {
     const int K = L.tile_levels - 1;
-    for (int v = tid; v < 2 * kPyrWarps * 256; v += kPyrThreads) (&sm.h01[0][0][0])[v] = 0;
-    for (int v = tid; v < (kTileLog2 - 1) * 256; v += kPyrThreads) (&sm.hs[0][0])[v] = 0;
-    __syncthreads();
-
-    pdl_trigger();
-    const int t0 = (int)(((long long)blockIdx.x * total_tiles) / gridDim.x);
-    const int t1 = (int)(((long long)(blockIdx.x + 1) * total_tiles) / gridDim.x);
-    auto origin = [&](int t, int *e, int *y0, int *x0) {
-        *e = t / tiles_per_exp;
-        const int rt = t - *e * tiles_per_exp;
-        const int ty = rt / tiles_x;
-        *y0 = ty * kTileRows;
-        *x0 = (rt - ty * tiles_x) * kTileCols;
-    };
+    const int tiles_y = tiles_per_exp / tiles_x;
+    TileCursor cc, nc;
+    cc.init(t0, tiles_x, tiles_per_exp);
+    nc = cc;
     TileRgb cur, nxt;
-    if (kAligned && t0 < t1) {
-        int e, y0, x0;
-        origin(t0, &e, &y0, &x0);
-        tile_load_rgb(images, L, e, y0, x0, min(kTileRows, L.h - y0), min(kTileCols, L.w - x0), cur);
+    if (t0 < t1) {
+        const int y0 = cc.ty * kTileRows, x0 = cc.tx * kTileCols;
+        tile_load_rgb(images, L, cc.e, y0, x0, min(kTileRows, L.h - y0), min(kTileCols, L.w - x0), cur);
     }
     int cur_e = -1, done = 0;
     bool waited = false;
+    uint8_t *ebase = ws;
     for (int t = t0; t < t1; ++t) {
-        int e, y0, x0;
-        origin(t, &e, &y0, &x0);
+        const int e = cc.e, y0 = cc.ty * kTileRows, x0 = cc.tx * kTileCols;
         if (e != cur_e) {
             if (cur_e >= 0) {
                 if (!waited) pdl_wait();  // the histograms were cleared by the previous kernel
@@ -66,33 +54,94 @@ k_pyramid(const uint8_t *__restrict__ images, const mtb_layout_t L, uint8_t *__r
             }
             cur_e = e;
             done = 0;
+            ebase = ws + (size_t)e * L.gray_exposure_stride;
         }
         const int rows = min(kTileRows, L.h - y0);
         const int cols = min(kTileCols, L.w - x0);
-        if (kAligned) {
-            tile_level0_loaded(cur, L, ws, e, y0, x0, rows, cols, sm);
-            if (t + 1 < t1) {  // in flight while levels 1..5 of this tile are built
-                int e1, y1, x1;
-                origin(t + 1, &e1, &y1, &x1);
-                tile_load_rgb(images, L, e1, y1, x1, min(kTileRows, L.h - y1), min(kTileCols, L.w - x1), nxt);
-            }
-        } else {
-            tile_level0_general(images, L, ws, e, y0, x0, rows, cols, sm);
+        const bool full = rows == kTileRows && cols == kTileCols;
+        uint8_t *lv2 = sm.lv + ((t - t0) & 1) * kLv2Bytes;
+        if (full) tile_levels012<true>(cur, L, ebase, y0, x0, rows, cols, K, sm, lv2);
+        else tile_levels012<false>(cur, L, ebase, y0, x0, rows, cols, K, sm, lv2);
+        nc.next(tiles_x, tiles_y);
+        if (t + 1 < t1) {
+            const int y1 = nc.ty * kTileRows, x1 = nc.tx * kTileCols;
+            tile_load_rgb(images, L, nc.e, y1, x1, min(kTileRows, L.h - y1), min(kTileCols, L.w - x1), nxt);
         }
+        __syncthreads();  // level 2 of the tile is in lv2
+        // lv2 is written again two tiles later, after the next barrier, which
+        // every warp passes only after its share of this tile's tail
+        const int a = (threadIdx.x >> 5) - (((t - t0) & 1) ? 4 : 0);
+        if (K >= 3 && a >= 0 && a < 4) {
+            if (full) tile_tail<true>(L, ebase, y0, x0, K, sm, lv2, a);
+            else tile_tail<false>(L, ebase, y0, x0, K, sm, lv2, a);
+        }
+        ++done;
+        cur = nxt;
+        cc = nc;
+    }
+    if (cur_e >= 0) {
+        if (!waited) pdl_wait();
+        flush_exposure(L, ws, cur_e, done, tiles_per_exp, K, sm);
+    }
+}
+
+// Any width: level 0 of each tile through shared memory (groups clipped to the
+// rows' pixel runs), then levels 1..5 from it.
+__device__ __forceinline__ void pyramid_general(const uint8_t *__restrict__ images, const mtb_layout_t &L,
+                                                uint8_t *__restrict__ ws, int tiles_x, int tiles_per_exp, int t0,
+                                                int t1, PyrShared &sm) {
+    const int K = L.tile_levels - 1;
+    int cur_e = -1, done = 0;
+    bool waited = false;
+    for (int t = t0; t < t1; ++t) {
+        const int e = t / tiles_per_exp;
+        const int rt = t - e * tiles_per_exp;
+        const int ty = rt / tiles_x;
+        const int y0 = ty * kTileRows, x0 = (rt - ty * tiles_x) * kTileCols;
+        if (e != cur_e) {
+            if (cur_e >= 0) {
+                if (!waited) pdl_wait();
+                waited = true;
+                flush_exposure(L, ws, cur_e, done, tiles_per_exp, K, sm);
+            }
+            cur_e = e;
+            done = 0;
+        }
+        const int rows = min(kTileRows, L.h - y0);
+        const int cols = min(kTileCols, L.w - x0);
+        tile_level0_general(images, L, ws, e, y0, x0, rows, cols, sm);
         __syncthreads();
-        if (!kAligned) tile_store_level0(L, ws, e, y0, x0, rows, cols, sm);
+        tile_store_level0(L, ws, e, y0, x0, rows, cols, sm);
         if (K >= 1) tile_levels12(L, ws, e, y0, x0, K, sm);
         __syncthreads();
         // levels 3..5, a 32-column block per warp; the next tile's level 0 only
         // writes level 0 of the shared buffer
         if (K >= 3) tile_block_tail(L, ws, e, y0, x0, K, sm);
         ++done;
-        if (kAligned) cur = nxt;
     }
     if (cur_e >= 0) {
         if (!waited) pdl_wait();
         flush_exposure(L, ws, cur_e, done, tiles_per_exp, K, sm);
     }
+}
+
+template <bool kAligned>
+__global__ void __launch_bounds__(kPyrThreads, kAligned ? 3 : 4)
+k_pyramid(const uint8_t *__restrict__ images, const mtb_layout_t L, uint8_t *__restrict__ ws, int tiles_x,
+          int tiles_per_exp, int total_tiles) {
+    static_assert(kPyrThreads == 256, "one thread per histogram bin in the flush");
+    static_assert(2 * kLv2Bytes <= kLvBytes, "two level-2 buffers fit the shared level buffer");
+    __shared__ PyrShared sm;
+    const int tid = threadIdx.x;
+    for (int v = tid; v < 2 * kPyrWarps * 256; v += kPyrThreads) (&sm.h01[0][0][0])[v] = 0;
+    for (int v = tid; v < (kTileLog2 - 1) * 256; v += kPyrThreads) (&sm.hs[0][0])[v] = 0;
+    __syncthreads();
+
+    pdl_trigger();
+    const int t0 = (int)(((long long)blockIdx.x * total_tiles) / gridDim.x);
+    const int t1 = (int)(((long long)(blockIdx.x + 1) * total_tiles) / gridDim.x);
+    if (kAligned) pyramid_aligned(images, L, ws, tiles_x, tiles_per_exp, t0, t1, sm);
+    else pyramid_general(images, L, ws, tiles_x, tiles_per_exp, t0, t1, sm);
 }
 
 // Clears n 32-bit words (the histograms and counters of a stack).

@@ -72,60 +72,27 @@ __device__ __forceinline__ uint32_t shrink2(uint32_t a, uint32_t b) {
     return (s >> 2) & 0x00ff00ffu;
 }
 
-// ---- level 0 of one tile: gray into shared memory (and global), histogram ----
-// W is a multiple of 16: every tile row is a whole number of aligned groups.
-__device__ __forceinline__ void tile_level0_aligned(const uint8_t *__restrict__ images, const mtb_layout_t &L,
-                                                    uint8_t *ws, int e, int y0, int x0, int rows, int cols,
-                                                    PyrShared &sm) {
-    const int tid = threadIdx.x;
-    const uint64_t W = (uint64_t)L.w;
-    const uint64_t e0 = (uint64_t)e * W * (uint64_t)L.h;
-    uint8_t *g0 = Planes::gray(ws, L, e, 0);
-    const size_t gp0 = (size_t)L.gray_pitch[0];
-    uint32_t *h0 = sm.h01[0][tid >> 5];
-    constexpr int kGroups = kTileRows * (kTileCols / 16);
-    constexpr int kPer = kGroups / kPyrThreads;
-    uint4 raw[kPer][3];
-    bool ok[kPer];
-#pragma unroll
-    for (int k = 0; k < kPer; ++k) {
-        const int grp = tid + k * kPyrThreads;
-        const int r = grp >> 4, c = (grp & 15) << 4;
-        ok[k] = r < rows && c < cols;
-        if (ok[k]) {
-            const uint4 *src = reinterpret_cast<const uint4 *>(images + 3 * (e0 + (uint64_t)(y0 + r) * W + x0 + c));
-            raw[k][0] = __ldcs(src);
-            raw[k][1] = __ldcs(src + 1);
-            raw[k][2] = __ldcs(src + 2);
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < kPer; ++k) {
-        if (!ok[k]) continue;
-        const int grp = tid + k * kPyrThreads;
-        const int r = grp >> 4, c = (grp & 15) << 4;
-        uint32_t g[16];
-        const uint4 v = gray16(raw[k][0], raw[k][1], raw[k][2], g);
-        *reinterpret_cast<uint4 *>(sm.lv + r * kTileCols + c) = v;
-        *reinterpret_cast<uint4 *>(g0 + (size_t)(y0 + r) * gp0 + x0 + c) = v;
-        hist_group(h0, g, v, 0, 16);
-    }
-}
+// ---- widths that are a multiple of 16 ----
+// Thread u of the CTA owns the 16-pixel column group cg = u % 16 of tile rows
+// 2j and 2j + 1 (j = u / 16): level 1 (row j, 8 pixels) comes from its own
+// registers, level 2 (row j / 2 = the warp) from one exchange with lane u ^ 16,
+// and levels 3..5 from shuffles inside a warp, so no level between 0 and 2
+// passes through shared memory and a tile needs one CTA barrier.
 
-// The same, split in two: the RGB of a tile loaded into registers (issued one
-// tile ahead), then level 0 made from them.
+// The RGB of the thread's two groups (2 x 48 bytes), loaded one tile ahead.
 struct TileRgb {
-    uint4 raw[kTileRows * (kTileCols / 16) / kPyrThreads][3];
+    uint4 raw[2][3];
 };
+
 __device__ __forceinline__ void tile_load_rgb(const uint8_t *__restrict__ images, const mtb_layout_t &L, int e,
                                               int y0, int x0, int rows, int cols, TileRgb &t) {
     const int tid = threadIdx.x;
+    const int j = tid >> 4, c = (tid & 15) << 4;
     const uint64_t W = (uint64_t)L.w;
     const uint64_t e0 = (uint64_t)e * W * (uint64_t)L.h;
 #pragma unroll
-    for (int k = 0; k < kTileRows * (kTileCols / 16) / kPyrThreads; ++k) {
-        const int grp = tid + k * kPyrThreads;
-        const int r = grp >> 4, c = (grp & 15) << 4;
+    for (int k = 0; k < 2; ++k) {
+        const int r = 2 * j + k;
         if (r < rows && c < cols) {
             const uint4 *src = reinterpret_cast<const uint4 *>(images + 3 * (e0 + (uint64_t)(y0 + r) * W + x0 + c));
             t.raw[k][0] = __ldcs(src);
@@ -134,24 +101,147 @@ __device__ __forceinline__ void tile_load_rgb(const uint8_t *__restrict__ images
         }
     }
 }
-__device__ __forceinline__ void tile_level0_loaded(const TileRgb &t, const mtb_layout_t &L, uint8_t *ws, int e,
-                                                   int y0, int x0, int rows, int cols, PyrShared &sm) {
-    const int tid = threadIdx.x;
-    uint8_t *g0 = Planes::gray(ws, L, e, 0);
-    const size_t gp0 = (size_t)L.gray_pitch[0];
-    uint32_t *h0 = sm.h01[0][tid >> 5];
+
+// Adds 1 to the shared-memory counter at 32-bit shared address `addr`.
+__device__ __forceinline__ void smem_count(uint32_t addr) {
+    asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(addr) : "memory");
+}
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+constexpr int kLv2Bytes = (kTileRows >> 2) * (kTileCols >> 2);  // level 2 of one tile: 8 x 64
+
+// Levels 0, 1 and 2 of the thread's groups.  `ebase`: exposure e's base in the
+// workspace (plane l at ebase + gray_offset[l]); level 2 also goes to lv2 for
+// the tail.  kFull: the tile lies inside the image, so is every pixel of its
+// levels 1..5 (2^5 divides the tile's sides), and no bound is checked.
+template <bool kFull>
+__device__ __forceinline__ void tile_levels012(const TileRgb &t, const mtb_layout_t &L, uint8_t *ebase, int y0,
+                                               int x0, int rows, int cols, int K, PyrShared &sm, uint8_t *lv2) {
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int j = tid >> 4, cg = tid & 15, c = cg << 4;
+    uint4 v[2];
+    {
+        uint8_t *g0 = ebase + L.gray_offset[0];
+        const size_t gp0 = (size_t)L.gray_pitch[0];
+        const uint32_t h0 = smem_addr(sm.h01[0][tid >> 5]);
 #pragma unroll
-    for (int k = 0; k < kTileRows * (kTileCols / 16) / kPyrThreads; ++k) {
-        const int grp = tid + k * kPyrThreads;
-        const int r = grp >> 4, c = (grp & 15) << 4;
-        if (r >= rows || c >= cols) continue;
-        uint32_t g[16];
-        const uint4 v = gray16(t.raw[k][0], t.raw[k][1], t.raw[k][2], g);
-        *reinterpret_cast<uint4 *>(sm.lv + r * kTileCols + c) = v;
-        *reinterpret_cast<uint4 *>(g0 + (size_t)(y0 + r) * gp0 + x0 + c) = v;
-        hist_group(h0, g, v, 0, 16);
+        for (int k = 0; k < 2; ++k) {
+            uint32_t g[16];
+            v[k] = gray16(t.raw[k][0], t.raw[k][1], t.raw[k][2], g);
+            const int r = 2 * j + k;
+            if (kFull || (r < rows && c < cols)) {
+                *reinterpret_cast<uint4 *>(g0 + (size_t)(y0 + r) * gp0 + x0 + c) = v[k];
+#pragma unroll
+                for (int q = 0; q < 16; ++q) smem_count(h0 + 4 * g[q]);
+            }
+        }
+    }
+    if (K < 1) return;
+    // level 1, row j, columns 8cg..8cg+7 (a pixel exists iff both its rows and
+    // both its columns do, so the level-1 bounds cover the garbage of groups
+    // that were not loaded)
+    const uint32_t w1a = __byte_perm(shrink2(v[0].x, v[1].x), shrink2(v[0].y, v[1].y), 0x6420u);
+    const uint32_t w1b = __byte_perm(shrink2(v[0].z, v[1].z), shrink2(v[0].w, v[1].w), 0x6420u);
+    {
+        const int W1 = L.width[1], H1 = L.height[1];
+        const int yl = (y0 >> 1) + j, xl = (x0 >> 1) + 8 * cg;
+        if (kFull || (yl < H1 && xl < W1)) {
+            const uint32_t h1 = smem_addr(sm.h01[1][tid >> 5]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (kFull || xl + q < W1) smem_count(h1 + 4 * __byte_perm(w1a, 0u, 0x4440u + q));
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (kFull || xl + 4 + q < W1) smem_count(h1 + 4 * __byte_perm(w1b, 0u, 0x4440u + q));
+        }
+        if (kFull || (yl < H1 && xl < L.gray_pitch[1]))  // 8 bytes inside the pitch (a multiple of 32)
+            *reinterpret_cast<uint2 *>(ebase + L.gray_offset[1] + (size_t)yl * L.gray_pitch[1] + xl) =
+                make_uint2(w1a, w1b);
+    }
+    if (K < 2) return;
+    // level 2, row m = warp: the top lane (level-1 row 2m) makes columns 4cg
+    // and 4cg + 1 from the first halves of both rows, the bottom lane 4cg + 2
+    // and 4cg + 3 from the second halves
+    const bool top = lane < 16;
+    const uint32_t recv = __shfl_xor_sync(0xffffffffu, top ? w1b : w1a, 16);
+    const uint32_t w2 = __byte_perm(top ? shrink2(w1a, recv) : shrink2(recv, w1b), 0u, 0x4420u);
+    const int m = tid >> 5, xc = 4 * cg + (top ? 0 : 2);
+    *reinterpret_cast<uint16_t *>(lv2 + m * (kTileCols >> 2) + xc) = (uint16_t)w2;
+    const int yl = (y0 >> 2) + m, xl = (x0 >> 2) + xc;
+    if (kFull || yl < L.height[2]) {
+        const int W2 = L.width[2];
+        const uint32_t hs = smem_addr(sm.hs[0]);
+        if (kFull || xl < W2) smem_count(hs + 4 * (w2 & 0xffu));
+        if (kFull || xl + 1 < W2) smem_count(hs + 4 * (w2 >> 8));
+        if (kFull || xl < L.gray_pitch[2])
+            *reinterpret_cast<uint16_t *>(ebase + L.gray_offset[2] + (size_t)yl * L.gray_pitch[2] + xl) = (uint16_t)w2;
     }
 }
+
+// Levels 3..K of the tile from lv2 by 4 warps: warp a (0..3) of the group
+// takes the 32-column blocks 2a (lanes 0-15) and 2a + 1 (lanes 16-31); lane
+// q = 4r + c of a half makes level-3 pixel (r, c) of its block, lanes with r
+// and c even add the 2x2 for level 4 by shuffles, lane 0 of the half level 5.
+template <bool kFull>
+__device__ __forceinline__ void tile_tail(const mtb_layout_t &L, uint8_t *ebase, int y0, int x0, int K,
+                                          PyrShared &sm, const uint8_t *lv2, int a) {
+    const int lane = threadIdx.x & 31;
+    const int b = 2 * a + (lane >> 4);
+    const int q = lane & 15, r = q >> 2, c = q & 3;
+    const uint32_t va = *reinterpret_cast<const uint16_t *>(lv2 + (2 * r) * (kTileCols >> 2) + 8 * b + 2 * c);
+    const uint32_t vb = *reinterpret_cast<const uint16_t *>(lv2 + (2 * r + 1) * (kTileCols >> 2) + 8 * b + 2 * c);
+    const uint32_t px3 = ((va & 0xffu) + (va >> 8) + (vb & 0xffu) + (vb >> 8) + 2u) >> 2;
+    {
+        const int yl = (y0 >> 3) + r, xl = (x0 >> 3) + 4 * b + c;
+        if (kFull || yl < L.height[3]) {
+            if (kFull || xl < L.width[3]) smem_count(smem_addr(sm.hs[1]) + 4 * px3);
+            if (kFull || xl < L.gray_pitch[3]) ebase[L.gray_offset[3] + (size_t)yl * L.gray_pitch[3] + xl] = (uint8_t)px3;
+        }
+    }
+    if (K < 4) return;
+    const uint32_t s1 = px3 + __shfl_down_sync(0xffffffffu, px3, 1);
+    const uint32_t s2 = s1 + __shfl_down_sync(0xffffffffu, s1, 4);
+    const uint32_t px4 = (s2 + 2u) >> 2;
+    {
+        const int yl = (y0 >> 4) + (r >> 1), xl = (x0 >> 4) + 2 * b + (c >> 1);
+        if ((q & 5) == 0 && (kFull || yl < L.height[4])) {
+            if (kFull || xl < L.width[4]) smem_count(smem_addr(sm.hs[2]) + 4 * px4);
+            if (kFull || xl < L.gray_pitch[4]) ebase[L.gray_offset[4] + (size_t)yl * L.gray_pitch[4] + xl] = (uint8_t)px4;
+        }
+    }
+    if (K < 5) return;
+    const uint32_t u1 = px4 + __shfl_down_sync(0xffffffffu, px4, 2);
+    const uint32_t u2 = u1 + __shfl_down_sync(0xffffffffu, u1, 8);
+    const uint32_t px5 = (u2 + 2u) >> 2;
+    {
+        const int yl = y0 >> 5, xl = (x0 >> 5) + b;
+        if (q == 0 && (kFull || yl < L.height[5])) {
+            if (kFull || xl < L.width[5]) smem_count(smem_addr(sm.hs[3]) + 4 * px5);
+            if (kFull || xl < L.gray_pitch[5]) ebase[L.gray_offset[5] + (size_t)yl * L.gray_pitch[5] + xl] = (uint8_t)px5;
+        }
+    }
+}
+
+// Position of tile t (exposure, tile row, tile column), advanced one tile at a
+// time so the loop divides by nothing.
+struct TileCursor {
+    int e, ty, tx;
+    __device__ __forceinline__ void init(int t, int tiles_x, int tiles_per_exp) {
+        e = t / tiles_per_exp;
+        const int rt = t - e * tiles_per_exp;
+        ty = rt / tiles_x;
+        tx = rt - ty * tiles_x;
+    }
+    __device__ __forceinline__ void next(int tiles_x, int tiles_y) {
+        if (++tx == tiles_x) {
+            tx = 0;
+            if (++ty == tiles_y) {
+                ty = 0;
+                ++e;
+            }
+        }
+    }
+};
 
 // Any W: the tile row's pixels are a flat run [p0, p0 + cols) that starts
 // anywhere inside a 16-pixel group, so groups are clipped to it.
