@@ -19,6 +19,8 @@
 // bytes because each byte of the minuend is >= 0x80).  The 4 MSBs of a word are
 // gathered into 4 adjacent bits by one multiply: bits 7, 15, 23, 31 times
 // 2^21 + 2^14 + 2^7 + 1 land on bits 28..31 without carries.
+// The exclusion test is that comparison on the per-byte absolute difference
+// |g - m| (__vabsdiffu4, a single SIMD instruction): eb = [|g - m| >= tol + 1].
 #include "mtb_bitmaps_dev.cuh"
 
 namespace mtb {

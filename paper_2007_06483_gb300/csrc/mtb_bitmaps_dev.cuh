@@ -24,14 +24,17 @@ struct ByteGE {
     }
 };
 
-// The thresholds of one (exposure, level): tb = [g >= m + 1], eb = [g < lo] or
-// [g >= hi + 1]; a test that can never hold is masked out instead.
+// The thresholds of one (exposure, level): tb = [g >= m + 1] and, since
+// g < m - tol or g > m + tol is |g - m| > tol, eb = [|g - m| >= tol + 1] on the
+// per-byte absolute difference (one SIMD instruction); a test that can never
+// hold (m = 255, tol = 255) is masked out instead.
 struct Thresholds {
-    ByteGE tb, lo, hi;
-    uint32_t tb_mask, hi_mask;
+    uint32_t m4;  // the median in every byte
+    ByteGE tb, eb;
+    uint32_t tb_mask, eb_mask;
     __device__ __forceinline__ Thresholds(int m, int tol)
-        : tb((uint32_t)min(m + 1, 255)), lo((uint32_t)max(m - tol, 0)), hi((uint32_t)min(m + tol + 1, 255)),
-          tb_mask(m < 255 ? kHi : 0u), hi_mask(m + tol < 255 ? kHi : 0u) {}
+        : m4((uint32_t)m * 0x01010101u), tb((uint32_t)min(m + 1, 255)), eb((uint32_t)min(tol + 1, 255)),
+          tb_mask(m < 255 ? kHi : 0u), eb_mask(tol < 255 ? kHi : 0u) {}
 };
 
 // MSBs of bytes 0..3 of x (already masked to kHi) -> bits 0..3.
@@ -44,7 +47,7 @@ __device__ __forceinline__ uint2 pack_bits(const uint32_t (&v)[8], const Thresho
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
         const uint32_t tm = th.tb(v[k]) & th.tb_mask;
-        const uint32_t em = (~th.lo(v[k]) | (th.hi(v[k]) & th.hi_mask)) & kHi;
+        const uint32_t em = th.eb(__vabsdiffu4(v[k], th.m4)) & th.eb_mask;
         // top nibble of the product holds the 4 flags; move it to bits 4k..4k+3
         const uint32_t pt = msb_nibble_top(tm), pe = msb_nibble_top(em);
         if (k == 7) {
@@ -125,7 +128,9 @@ __device__ __forceinline__ void bitmap_chunk_of(const mtb_layout_t &L, int item,
 }
 
 // Chunk c of level l (a tile level) of exposure e: threshold against the
-// median from the pyramid pass, pack, and count the chunk as done.
+// median from the pyramid pass, pack, and count the chunk as done.  Thread t
+// takes words c * chunk_words + t, + blockDim, ...; their (row, word) positions
+// advance by a fixed step, so only the first is a division.
 __device__ void bitmap_chunk(const mtb_layout_t &L, uint8_t *ws, int tol, int e, int l, int c, int chunk_words,
                              int *s_med) {
     constexpr int kGroup = 4;  // words whose gray loads a thread issues together
@@ -134,42 +139,48 @@ __device__ void bitmap_chunk(const mtb_layout_t &L, uint8_t *ws, int tol, int e,
     uint2 *__restrict__ out = Planes::bits(ws, L, e, l);
     const int words = bp * Hl;
     const int w_end = min(words, (c + 1) * chunk_words);
+    const int step = (int)blockDim.x, step_y = step / bp, step_q = step - step_y * bp;
+    int i0 = c * chunk_words + (int)threadIdx.x;
+    int y = i0 / bp, q = i0 - y * bp;  // position of word i0
     uint4 va[kGroup], vb[kGroup];
+    int xs[kGroup];  // first pixel of each word (the word index itself is idx: rows are bp words)
     // the gray loads of a group are issued before any store (and the first
     // group's before the median is read), so they are all in flight together
-    auto load_group = [&](int i0) {
+    auto load_group = [&]() {
 #pragma unroll
         for (int j = 0; j < kGroup; ++j) {
-            const int idx = i0 + j * (int)blockDim.x;
+            const int idx = i0 + j * step;
+            xs[j] = q * 32;
             va[j] = vb[j] = make_uint4(0u, 0u, 0u, 0u);
-            if (idx < w_end) {
-                const int y = idx / bp, x = (idx - y * bp) * 32;
-                if (x < Wl) {
-                    const uint4 *p = reinterpret_cast<const uint4 *>(g + (size_t)y * gpl + x);
-                    va[j] = __ldcs(p);
-                    vb[j] = __ldcs(p + 1);
-                }
+            if (idx < w_end && xs[j] < Wl) {
+                const uint4 *p = reinterpret_cast<const uint4 *>(g + (size_t)y * gpl + xs[j]);
+                va[j] = __ldcs(p);
+                vb[j] = __ldcs(p + 1);
+            }
+            q += step_q;
+            y += step_y;
+            if (q >= bp) {
+                q -= bp;
+                ++y;
             }
         }
     };
-    int i0 = c * chunk_words + (int)threadIdx.x;
-    load_group(i0);
+    load_group();
     if (threadIdx.x == 0) *s_med = *Planes::median(ws, L, e, l);
     __syncthreads();
     const Thresholds th(*s_med, tol);
     for (;;) {
 #pragma unroll
         for (int j = 0; j < kGroup; ++j) {
-            const int idx = i0 + j * (int)blockDim.x;
+            const int idx = i0 + j * step;
             if (idx < w_end) {
-                const int y = idx / bp, x = (idx - y * bp) * 32;
                 const uint32_t v[8] = {va[j].x, va[j].y, va[j].z, va[j].w, vb[j].x, vb[j].y, vb[j].z, vb[j].w};
-                out[idx] = x < Wl ? pack_bits(v, th, min(32, Wl - x)) : make_uint2(0u, 0u);
+                out[idx] = xs[j] < Wl ? pack_bits(v, th, min(32, Wl - xs[j])) : make_uint2(0u, 0u);
             }
         }
-        i0 += kGroup * (int)blockDim.x;
+        i0 += kGroup * step;
         if (i0 >= w_end) break;
-        load_group(i0);
+        load_group();
     }
     cta_signal(Ctr::bit_done(ws, L, e, l));
 }
