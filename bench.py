@@ -362,14 +362,17 @@ def run_gb300(args):
     if not args.no_e2e:
         host = images.cpu().pin_memory()
         dws = torch.empty(mtb.host_workspace_bytes(n, w, h, L), dtype=torch.uint8, device=dev)
+        host_out = torch.empty((n, 2), dtype=torch.int32, pin_memory=True)
         for _ in range(2):
-            mtb.align_stack_host(host, L, spec.noise_tol, spec.ref, device_workspace=dws, stream=stream)
+            mtb.align_stack_host(host, L, spec.noise_tol, spec.ref, device_workspace=dws, out=host_out,
+                                 stream=stream)
         Ke = max(3, min(K, 20))
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         barrier(world)
         e0.record(stream)
         for _ in range(Ke):
-            out = mtb.align_stack_host(host, L, spec.noise_tol, spec.ref, device_workspace=dws, stream=stream)
+            out = mtb.align_stack_host(host, L, spec.noise_tol, spec.ref, device_workspace=dws, out=host_out,
+                                       stream=stream)
         e1.record(stream)
         torch.cuda.synchronize(dev)
         e_ms = max_over_ranks(e0.elapsed_time(e1) / Ke, world, dev)
@@ -803,10 +806,12 @@ def run_paper(args):
         dws = torch.empty(mtb.host_workspace_bytes(n, w, h, L), dtype=torch.uint8, device=dev)
         qws = torch.empty(mtb.lib().mtb_quadrant_workspace_bytes(n, w, h, L - 1), dtype=torch.uint8, device=dev)
         out = torch.empty((n, 2), dtype=torch.int32, device=dev)
+        host_out = torch.empty((n, 2), dtype=torch.int32, pin_memory=True)
         moved = torch.empty_like(imgs)
         t = {}
         t["e2e_ms"] = _time_calls(lambda: mtb.align_stack_host(host, L, spec.noise_tol, spec.ref,
-                                                               device_workspace=dws, stream=stream), K, W, stream, dev)
+                                                               device_workspace=dws, out=host_out, stream=stream),
+                                  K, W, stream, dev)
         t["device_ms"] = _time_calls(lambda: mtb.align_stack(imgs, L, spec.noise_tol, spec.ref, workspace=ws, out=out,
                                                              stream=stream), K, W, stream, dev)
         t["chain_ms"] = _time_calls(lambda: mtb.align_stack_chain(imgs, L, spec.noise_tol, spec.ref, workspace=ws,

@@ -189,10 +189,16 @@ size_t mtb_host_workspace_bytes(int n_exposures, int w, int h, int levels);
 
 /* Align a stack held in HOST memory (Sec. III-B: the exposures are copied to the
  * device once).  host_images: host [n][h][w][3] uint8 (pinned memory lets the
- * copy run asynchronously); host_shifts_out: host int32 [n][2].  The copy in,
- * the alignment and the copy out are enqueued on `stream`, and the call returns
- * after synchronising it.  device_workspace: device, 256-byte aligned,
- * >= mtb_host_workspace_bytes(...) bytes, or NULL to allocate stream-ordered. */
+ * copy run asynchronously); host_shifts_out: host int32 [n][2].  Stacks of 8 MB
+ * or more are copied in bands of whole 32-row tile rows of one exposure (about
+ * 16 MB each) on a copy stream the library owns, one per device; the pyramid
+ * pass over each band runs on `stream` as soon as the band has landed, after
+ * work enqueued earlier on `stream`.  Smaller stacks are copied in one piece on
+ * `stream`.  The alignment and the copy out are enqueued on `stream`, and the
+ * call returns after synchronising it.  device_workspace: device, 256-byte
+ * aligned, >= mtb_host_workspace_bytes(...) bytes, or NULL to allocate
+ * stream-ordered.  Thread-safe; calls from several threads share the copy
+ * stream, so their copies run one after another. */
 int mtb_align_stack_host(const uint8_t *host_images, int n_exposures, int w, int h, int levels,
                          int noise_tol, int ref_idx, int32_t *host_shifts_out,
                          void *device_workspace, size_t device_workspace_bytes, void *stream);

@@ -302,14 +302,19 @@ def workspace_status(workspace, n: int, w: int, h: int, levels: int, stream=None
 
 
 def align_stack_host(images, levels: int, noise_tol: int = 4, ref_idx: int = 0, *, device_workspace=None,
-                     stream=None):
+                     out=None, stream=None):
     """Align a host [n, h, w, 3] uint8 stack (torch CPU tensor, ideally pinned);
-    copies in, aligns and copies the shifts back.  Returns int32 [n, 2] (CPU)."""
+    copies in, aligns and copies the shifts back.  Returns int32 [n, 2] (CPU):
+    `out` if given (a contiguous host int32 [n, 2] tensor), else a new one, pinned
+    when the images are."""
     import torch
 
     n, w, h = _dims(images)
-    out = torch.empty((n, 2), dtype=torch.int32).pin_memory() if images.is_pinned() else \
-        torch.empty((n, 2), dtype=torch.int32)
+    if out is None:
+        out = torch.empty((n, 2), dtype=torch.int32, pin_memory=images.is_pinned())
+    elif out.device.type != "cpu" or out.dtype != torch.int32 or tuple(out.shape) != (n, 2) or \
+            not out.is_contiguous():
+        raise ValueError("out must be a contiguous host int32 [n, 2] tensor")
     ws_ptr, ws_bytes = None, 0
     if device_workspace is not None:
         ws_ptr, ws_bytes = device_workspace.data_ptr(), device_workspace.numel()

@@ -1,6 +1,7 @@
 // mtb_api.cu -- the C ABI declared in include/mtb.h: argument checks, the
 // workspace layout and the entry points that enqueue the three stages.
 #include <cstring>
+#include <mutex>
 
 #include "mtb_internal.cuh"
 
@@ -106,6 +107,98 @@ int run_all(const uint8_t *images, const mtb_layout_t &L, int tol, int ref, uint
     rc = cuda_status(launch_bitmaps(L, tol, ws, s, true));
     if (rc != MTB_OK) return rc;
     return cuda_status(launch_search(L, ref, ws, shifts_out, level_errs_out, level_shifts_out, s, true, true, chain));
+}
+
+
+// ---- host-buffer entry: the copy in, in row bands, overlapped with the pyramid ----
+// The RGB is copied in bands of whole tile rows of one exposure on a copy
+// stream the library owns (one per device); after each band's copy the
+// pyramid pass over that band's tiles is launched on the caller's stream, so
+// only the last band's pyramid, the bitmaps and the search follow the copy.
+constexpr int kMaxBands = 32;
+constexpr size_t kBandBytes = 16u << 20;  // target bytes per band copy
+constexpr size_t kBandMinStack = 8u << 20;  // smaller stacks are copied in one piece
+
+struct CopyPipe {
+    std::mutex mu;  // held while a call enqueues (its events are reused by the next call)
+    bool ready = false;
+    cudaStream_t copy = nullptr;
+    cudaEvent_t start = nullptr;
+    cudaEvent_t band[kMaxBands] = {};
+};
+CopyPipe g_pipes[64];
+std::mutex g_pipes_mu;
+
+// The calling thread's device's pipe, created on first use; nullptr on error.
+CopyPipe *copy_pipe() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    CopyPipe &p = g_pipes[dev];
+    std::lock_guard<std::mutex> g(g_pipes_mu);
+    if (!p.ready) {
+        if (cudaStreamCreateWithFlags(&p.copy, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+        if (cudaEventCreateWithFlags(&p.start, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+        for (int k = 0; k < kMaxBands; ++k)
+            if (cudaEventCreateWithFlags(&p.band[k], cudaEventDisableTiming) != cudaSuccess) return nullptr;
+        p.ready = true;
+    }
+    return &p;
+}
+
+// Bands of tile rows per exposure: about kBandBytes each, at most kMaxBands in
+// all; 0 when the stack is copied in one piece.
+int bands_per_exposure(const mtb_layout_t &L, size_t img_bytes) {
+    if (img_bytes < kBandMinStack) return 0;
+    const long long tile_rows = (L.h + kTileRows - 1) / kTileRows;
+    const size_t exp_bytes = img_bytes / L.n;
+    long long b = (long long)((exp_bytes + kBandBytes / 2) / kBandBytes);
+    if (b < 1) b = 1;
+    if (b > tile_rows) b = tile_rows;
+    while (b > 1 && b * L.n > kMaxBands) --b;
+    return b * L.n > kMaxBands ? 0 : (int)b;
+}
+
+// Enqueues the banded copy of host_images into d_img and, on s, the clear and
+// the pyramid pass band by band; the bitmaps and search are chained after.  On
+// a failure after the first copy, waits for the copies so that the caller may
+// release the device buffer.
+int enqueue_banded(const uint8_t *host_images, uint8_t *d_img, const mtb_layout_t &L, int bands, uint8_t *ws,
+                   cudaStream_t s) {
+    CopyPipe *p = copy_pipe();
+    if (!p) return MTB_ERR_CUDA;
+    std::lock_guard<std::mutex> g(p->mu);
+    const long long tile_rows = (L.h + kTileRows - 1) / kTileRows;
+    const long long tiles_x = (L.w + kTileCols - 1) / kTileCols;
+    const long long per_exp = pyramid_tiles_per_exposure(L);
+    const size_t row_bytes = (size_t)L.w * 3;
+    // the copy must not overwrite the device images while earlier work on s
+    // (a previous call on the same workspace) may still read them
+    if (cudaEventRecord(p->start, s) != cudaSuccess || cudaStreamWaitEvent(p->copy, p->start, 0) != cudaSuccess)
+        return MTB_ERR_CUDA;
+    auto fail = [&]() {
+        cudaStreamSynchronize(p->copy);
+        return MTB_ERR_CUDA;
+    };
+    int k = 0;
+    for (int e = 0; e < L.n; ++e)
+        for (int b = 0; b < bands; ++b, ++k) {
+            const long long r0 = tile_rows * b / bands, r1 = tile_rows * (b + 1) / bands;
+            const size_t y0 = (size_t)r0 * kTileRows, y1 = (size_t)(r1 * kTileRows < L.h ? r1 * kTileRows : L.h);
+            const size_t off = ((size_t)e * L.h + y0) * row_bytes, len = (y1 - y0) * row_bytes;
+            if (cudaMemcpyAsync(d_img + off, host_images + off, len, cudaMemcpyHostToDevice, p->copy) != cudaSuccess ||
+                cudaEventRecord(p->band[k], p->copy) != cudaSuccess)
+                return fail();
+        }
+    if (launch_clear_stack(L, ws, s) != cudaSuccess) return fail();
+    k = 0;
+    for (int e = 0; e < L.n; ++e)
+        for (int b = 0; b < bands; ++b, ++k) {
+            const long long r0 = tile_rows * b / bands, r1 = tile_rows * (b + 1) / bands;
+            if (cudaStreamWaitEvent(s, p->band[k], 0) != cudaSuccess) return fail();
+            const long long t0 = e * per_exp + r0 * tiles_x, t1 = e * per_exp + r1 * tiles_x;
+            if (launch_pyramid_range(d_img, L, ws, t0, t1, s, false) != cudaSuccess) return fail();
+        }
+    return MTB_OK;
 }
 
 bool misaligned(const void *p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) != 0; }
@@ -294,8 +387,16 @@ int mtb_align_stack_host(const uint8_t *host_images, int n_exposures, int w, int
     uint8_t *d_img = base;
     uint8_t *ws = base + align_up(img_bytes, 256);
     int32_t *d_shifts = reinterpret_cast<int32_t *>(ws + L.total_bytes);
-    rc = cuda_status(cudaMemcpyAsync(d_img, host_images, img_bytes, cudaMemcpyHostToDevice, s));
-    if (rc == MTB_OK) rc = run_all(d_img, L, noise_tol, ref_idx, ws, d_shifts, nullptr, nullptr, s);
+    const int bands = bands_per_exposure(L, img_bytes);
+    if (bands > 0) {
+        rc = enqueue_banded(host_images, d_img, L, bands, ws, s);
+        if (rc == MTB_OK) rc = cuda_status(launch_bitmaps(L, noise_tol, ws, s, true));
+        if (rc == MTB_OK)
+            rc = cuda_status(launch_search(L, ref_idx, ws, d_shifts, nullptr, nullptr, s, true, true, false));
+    } else {
+        rc = cuda_status(cudaMemcpyAsync(d_img, host_images, img_bytes, cudaMemcpyHostToDevice, s));
+        if (rc == MTB_OK) rc = run_all(d_img, L, noise_tol, ref_idx, ws, d_shifts, nullptr, nullptr, s);
+    }
     if (rc == MTB_OK)
         rc = cuda_status(cudaMemcpyAsync(host_shifts_out, d_shifts, (size_t)n_exposures * 2 * sizeof(int32_t),
                                          cudaMemcpyDeviceToHost, s));

@@ -102,6 +102,13 @@ int check_stack_args(int n, int w, int h, int levels, int noise_tol, int ref_idx
 // same call, so its first kernel may overlap that stage's tail (programmatic
 // dependent launch).  A stage called on its own starts after all earlier work.
 cudaError_t launch_pyramid(const uint8_t *images, const mtb_layout_t &L, uint8_t *ws, cudaStream_t s);
+// The parts of launch_pyramid: clearing the stack's bookkeeping, and the
+// pyramid pass over tiles [tile_begin, tile_end) (tile t is tile t % per_exp,
+// row-major, of exposure t / per_exp; launch_pyramid covers them all).
+cudaError_t launch_clear_stack(const mtb_layout_t &L, uint8_t *ws, cudaStream_t s);
+long long pyramid_tiles_per_exposure(const mtb_layout_t &L);
+cudaError_t launch_pyramid_range(const uint8_t *images, const mtb_layout_t &L, uint8_t *ws, long long tile_begin,
+                                 long long tile_end, cudaStream_t s, bool chained);
 cudaError_t launch_bitmaps(const mtb_layout_t &L, int noise_tol, uint8_t *ws, cudaStream_t s, bool chained);
 cudaError_t launch_apply_shifts(const uint8_t *images, int n, int w, int h, const int32_t *shifts, int fill,
                                 uint8_t *out, cudaStream_t s);

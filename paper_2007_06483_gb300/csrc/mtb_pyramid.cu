@@ -128,7 +128,7 @@ __device__ __forceinline__ void pyramid_general(const uint8_t *__restrict__ imag
 template <bool kAligned>
 __global__ void __launch_bounds__(kPyrThreads, kAligned ? 3 : 4)
 k_pyramid(const uint8_t *__restrict__ images, const mtb_layout_t L, uint8_t *__restrict__ ws, int tiles_x,
-          int tiles_per_exp, int total_tiles) {
+          int tiles_per_exp, int tile_begin, int tile_count) {
     static_assert(kPyrThreads == 256, "one thread per histogram bin in the flush");
     static_assert(2 * kLv2Bytes <= kLvBytes, "two level-2 buffers fit the shared level buffer");
     __shared__ PyrShared sm;
@@ -138,8 +138,10 @@ k_pyramid(const uint8_t *__restrict__ images, const mtb_layout_t L, uint8_t *__r
     __syncthreads();
 
     pdl_trigger();
-    const int t0 = (int)(((long long)blockIdx.x * total_tiles) / gridDim.x);
-    const int t1 = (int)(((long long)(blockIdx.x + 1) * total_tiles) / gridDim.x);
+    // tiles [tile_begin, tile_begin + tile_count) of the stack (all of them, or
+    // the rows of one exposure whose copy has landed), split into runs
+    const int t0 = tile_begin + (int)(((long long)blockIdx.x * tile_count) / gridDim.x);
+    const int t1 = tile_begin + (int)(((long long)(blockIdx.x + 1) * tile_count) / gridDim.x);
     if (kAligned) pyramid_aligned(images, L, ws, tiles_x, tiles_per_exp, t0, t1, sm);
     else pyramid_general(images, L, ws, tiles_x, tiles_per_exp, t0, t1, sm);
 }
@@ -153,12 +155,7 @@ int g_pyr_blocks_per_sm[2] = {0, 0};
 
 }  // namespace
 
-cudaError_t launch_pyramid(const uint8_t *images, const mtb_layout_t &L, uint8_t *ws, cudaStream_t s) {
-    const int tiles_x = (L.w + kTileCols - 1) / kTileCols;
-    const int tiles_y = (L.h + kTileRows - 1) / kTileRows;
-    const long long per_exp = (long long)tiles_x * tiles_y;
-    const long long total = per_exp * L.n;
-    if (total > 0x7fffffffLL) return cudaErrorInvalidValue;
+cudaError_t launch_clear_stack(const mtb_layout_t &L, uint8_t *ws, cudaStream_t s) {
     // everything after the bit planes (histograms, counters, errors, medians,
     // bases, shifts, window tables, status) is small and adjacent: one launch
     // clears it, so that a search chained to this pyramid needs no clearing of
@@ -167,25 +164,45 @@ cudaError_t launch_pyramid(const uint8_t *images, const mtb_layout_t &L, uint8_t
     const long long cap = 4ll * device_sm_count();
     const long long blocks = (words + 1023) / 1024 < cap ? (words + 1023) / 1024 : cap;
     if (words > 0x7fffffffLL) return cudaErrorInvalidValue;
-    cudaError_t err = launch_k(k_clear, dim3((unsigned)blocks), dim3(256), s, false,
-                               reinterpret_cast<uint32_t *>(ws + L.hist_offset), (int)words);
-    if (err != cudaSuccess) return err;
+    return launch_k(k_clear, dim3((unsigned)blocks), dim3(256), s, false,
+                    reinterpret_cast<uint32_t *>(ws + L.hist_offset), (int)words);
+}
+
+long long pyramid_tiles_per_exposure(const mtb_layout_t &L) {
+    return (long long)((L.w + kTileCols - 1) / kTileCols) * ((L.h + kTileRows - 1) / kTileRows);
+}
+
+cudaError_t launch_pyramid_range(const uint8_t *images, const mtb_layout_t &L, uint8_t *ws, long long tile_begin,
+                                 long long tile_end, cudaStream_t s, bool chained) {
+    const int tiles_x = (L.w + kTileCols - 1) / kTileCols;
+    const long long per_exp = pyramid_tiles_per_exposure(L);
+    const long long total = per_exp * L.n;
+    if (total > 0x7fffffffLL || tile_begin < 0 || tile_end > total || tile_begin >= tile_end)
+        return cudaErrorInvalidValue;
     const bool aligned = (L.w % 16) == 0;
     int &nb = g_pyr_blocks_per_sm[aligned ? 1 : 0];
     if (nb == 0) {
         int v = 0;
-        err = aligned ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_pyramid<true>, kPyrThreads, 0)
-                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_pyramid<false>, kPyrThreads, 0);
+        const cudaError_t err =
+            aligned ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_pyramid<true>, kPyrThreads, 0)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_pyramid<false>, kPyrThreads, 0);
         if (err != cudaSuccess) return err;
         nb = v > 0 ? v : 1;
     }
+    const long long count = tile_end - tile_begin;
     const long long cap_p = (long long)device_sm_count() * nb;
-    const int grid = (int)(total < cap_p ? total : cap_p);
+    const int grid = (int)(count < cap_p ? count : cap_p);
     if (aligned)
-        return launch_k(k_pyramid<true>, dim3(grid), dim3(kPyrThreads), s, true, images, L, ws, tiles_x, (int)per_exp,
-                        (int)total);
-    return launch_k(k_pyramid<false>, dim3(grid), dim3(kPyrThreads), s, true, images, L, ws, tiles_x, (int)per_exp,
-                    (int)total);
+        return launch_k(k_pyramid<true>, dim3(grid), dim3(kPyrThreads), s, chained, images, L, ws, tiles_x,
+                        (int)per_exp, (int)tile_begin, (int)count);
+    return launch_k(k_pyramid<false>, dim3(grid), dim3(kPyrThreads), s, chained, images, L, ws, tiles_x,
+                    (int)per_exp, (int)tile_begin, (int)count);
+}
+
+cudaError_t launch_pyramid(const uint8_t *images, const mtb_layout_t &L, uint8_t *ws, cudaStream_t s) {
+    const cudaError_t err = launch_clear_stack(L, ws, s);
+    if (err != cudaSuccess) return err;
+    return launch_pyramid_range(images, L, ws, 0, pyramid_tiles_per_exposure(L) * L.n, s, true);
 }
 
 }  // namespace mtb

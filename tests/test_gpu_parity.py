@@ -109,8 +109,8 @@ def test_one_call_matches_stages(mtb_lib, oracle_mod):
     imgs = synth.make_stack(spec, "cuda")
     shifts, errs, lsh = mtb_lib.align_stack(imgs, spec.levels, 4, spec.ref, level_outputs=True)
     plain = mtb_lib.align_stack(imgs, spec.levels, 4, spec.ref)
-    host = mtb_lib.align_stack_host(imgs.cpu().pin_memory(), spec.levels, 4, spec.ref)  # read in place
-    paged = mtb_lib.align_stack_host(imgs.cpu().contiguous(), spec.levels, 4, spec.ref)  # copied first
+    host = mtb_lib.align_stack_host(imgs.cpu().pin_memory(), spec.levels, 4, spec.ref)  # pinned
+    paged = mtb_lib.align_stack_host(imgs.cpu().contiguous(), spec.levels, 4, spec.ref)  # pageable
     torch.cuda.synchronize()
     want = oracle_mod.align_stack(imgs.cpu().numpy(), spec.levels, 4, spec.ref)
     assert np.array_equal(errs.cpu().numpy().view(np.uint32), want["level_errs"])
