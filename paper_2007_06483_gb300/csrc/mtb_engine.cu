@@ -125,8 +125,13 @@ __device__ __noinline__ void pyr_item(const StackDesc &d, int k, EngineShared &s
             uint8_t *lv2 = sm.pyr.lv + ((t - t0) & 1) * kLv2Bytes;
             TileRgb rgb;
             tile_load_rgb(images, L, e, y0, x0, rows, cols, rgb);
-            if (full) tile_levels012<true>(rgb, L, ebase, y0, x0, rows, cols, K, sm.pyr, lv2);
-            else tile_levels012<false>(rgb, L, ebase, y0, x0, rows, cols, K, sm.pyr, lv2);
+            uint4 v[2];
+            if (full) tile_level0<true>(rgb, L, ebase, y0, x0, rows, cols, sm.pyr, v);
+            else tile_level0<false>(rgb, L, ebase, y0, x0, rows, cols, sm.pyr, v);
+            if (K >= 1) {
+                if (full) tile_levels12_pair<true>(v, L, ebase, y0, x0, K, sm.pyr, lv2);
+                else tile_levels12_pair<false>(v, L, ebase, y0, x0, K, sm.pyr, lv2);
+            }
             __syncthreads();
             const int a = (threadIdx.x >> 5) - (((t - t0) & 1) ? 4 : 0);
             if (K >= 3 && a >= 0 && a < 4) {
@@ -263,6 +268,7 @@ __global__ void __launch_bounds__(kEngineThreads, 4) k_engine(const EngineArgs A
 // engine's queue head.  One CTA per stack.
 template <bool kBatch>
 __global__ void k_engine_clear(const EngineArgs A) {
+    pdl_trigger();  // k_engine waits (griddepcontrol.wait) before it touches anything cleared here
     const StackDesc &d = kBatch ? A.stacks[blockIdx.x] : A.single;
     const mtb_layout_t &L = d.L;
     uint8_t *ws = d.ws;

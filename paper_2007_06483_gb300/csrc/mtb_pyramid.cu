@@ -23,11 +23,12 @@
 namespace mtb {
 namespace {
 
-// Widths that are a multiple of 16.  The next tile's RGB is loaded into
-// registers (3 CTAs per SM leave room for it) while levels 0..2 of the current
-// one are built; after the tile's one barrier, levels 3..5 are built by half of
-// the warps (alternating with the tile, from one of two level-2 buffers) while
-// the others go on.
+// Widths that are a multiple of 16.  Once level 0 of the current tile has
+// consumed its RGB, the next tile's RGB is loaded into the same registers (3
+// CTAs per SM leave room for it) and stays in flight while levels 1..5 are
+// built; after the tile's one barrier, levels 3..5 are built by half of the
+// warps (alternating with the tile, from one of two level-2 buffers) while the
+// others go on.
 __device__ __forceinline__ void pyramid_aligned(const uint8_t *__restrict__ images, const mtb_layout_t &L,
                                                 uint8_t *__restrict__ ws, int tiles_x, int tiles_per_exp, int t0,
                                                 int t1, PyrShared &sm) {
@@ -60,12 +61,19 @@ __device__ __forceinline__ void pyramid_aligned(const uint8_t *__restrict__ imag
         const int cols = min(kTileCols, L.w - x0);
         const bool full = rows == kTileRows && cols == kTileCols;
         uint8_t *lv2 = sm.lv + ((t - t0) & 1) * kLv2Bytes;
-        if (full) tile_levels012<true>(cur, L, ebase, y0, x0, rows, cols, K, sm, lv2);
-        else tile_levels012<false>(cur, L, ebase, y0, x0, rows, cols, K, sm, lv2);
+        uint4 v[2];
+        if (full) tile_level0<true>(cur, L, ebase, y0, x0, rows, cols, sm, v);
+        else tile_level0<false>(cur, L, ebase, y0, x0, rows, cols, sm, v);
+        // the current tile's RGB is consumed: its registers take the next one,
+        // in flight while levels 1..5 are built
         nc.next(tiles_x, tiles_y);
         if (t + 1 < t1) {
             const int y1 = nc.ty * kTileRows, x1 = nc.tx * kTileCols;
             tile_load_rgb(images, L, nc.e, y1, x1, min(kTileRows, L.h - y1), min(kTileCols, L.w - x1), nxt);
+        }
+        if (K >= 1) {
+            if (full) tile_levels12_pair<true>(v, L, ebase, y0, x0, K, sm, lv2);
+            else tile_levels12_pair<false>(v, L, ebase, y0, x0, K, sm, lv2);
         }
         __syncthreads();  // level 2 of the tile is in lv2
         // lv2 is written again two tiles later, after the next barrier, which
@@ -147,7 +155,10 @@ k_pyramid(const uint8_t *__restrict__ images, const mtb_layout_t L, uint8_t *__r
 }
 
 // Clears n 32-bit words (the histograms and counters of a stack).
+// The pyramid pass chained after it may start at once: it writes only gray
+// planes before its griddepcontrol.wait, and nothing this kernel clears.
 __global__ void k_clear(uint32_t *p, int n) {
+    pdl_trigger();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = 0;
 }
 

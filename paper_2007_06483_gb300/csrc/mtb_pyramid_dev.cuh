@@ -110,33 +110,39 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)
 
 constexpr int kLv2Bytes = (kTileRows >> 2) * (kTileCols >> 2);  // level 2 of one tile: 8 x 64
 
-// Levels 0, 1 and 2 of the thread's groups.  `ebase`: exposure e's base in the
-// workspace (plane l at ebase + gray_offset[l]); level 2 also goes to lv2 for
-// the tail.  kFull: the tile lies inside the image, so is every pixel of its
-// levels 1..5 (2^5 divides the tile's sides), and no bound is checked.
+// Level 0 of the thread's groups: gray, stored and counted; v gets the packed
+// gray words (row 2j, row 2j + 1) for levels 1 and 2.  `ebase`: exposure e's
+// base in the workspace (plane l at ebase + gray_offset[l]).  kFull: the tile
+// lies inside the image, so is every pixel of its levels 1..5 (2^5 divides the
+// tile's sides), and no bound is checked.
 template <bool kFull>
-__device__ __forceinline__ void tile_levels012(const TileRgb &t, const mtb_layout_t &L, uint8_t *ebase, int y0,
-                                               int x0, int rows, int cols, int K, PyrShared &sm, uint8_t *lv2) {
-    const int tid = threadIdx.x, lane = tid & 31;
-    const int j = tid >> 4, cg = tid & 15, c = cg << 4;
-    uint4 v[2];
-    {
-        uint8_t *g0 = ebase + L.gray_offset[0];
-        const size_t gp0 = (size_t)L.gray_pitch[0];
-        const uint32_t h0 = smem_addr(sm.h01[0][tid >> 5]);
+__device__ __forceinline__ void tile_level0(const TileRgb &t, const mtb_layout_t &L, uint8_t *ebase, int y0, int x0,
+                                            int rows, int cols, PyrShared &sm, uint4 (&v)[2]) {
+    const int tid = threadIdx.x;
+    const int j = tid >> 4, c = (tid & 15) << 4;
+    uint8_t *g0 = ebase + L.gray_offset[0];
+    const size_t gp0 = (size_t)L.gray_pitch[0];
+    const uint32_t h0 = smem_addr(sm.h01[0][tid >> 5]);
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            uint32_t g[16];
-            v[k] = gray16(t.raw[k][0], t.raw[k][1], t.raw[k][2], g);
-            const int r = 2 * j + k;
-            if (kFull || (r < rows && c < cols)) {
-                *reinterpret_cast<uint4 *>(g0 + (size_t)(y0 + r) * gp0 + x0 + c) = v[k];
+    for (int k = 0; k < 2; ++k) {
+        uint32_t g[16];
+        v[k] = gray16(t.raw[k][0], t.raw[k][1], t.raw[k][2], g);
+        const int r = 2 * j + k;
+        if (kFull || (r < rows && c < cols)) {
+            *reinterpret_cast<uint4 *>(g0 + (size_t)(y0 + r) * gp0 + x0 + c) = v[k];
 #pragma unroll
-                for (int q = 0; q < 16; ++q) smem_count(h0 + 4 * g[q]);
-            }
+            for (int q = 0; q < 16; ++q) smem_count(h0 + 4 * g[q]);
         }
     }
-    if (K < 1) return;
+}
+
+// Levels 1 and 2 of the thread's groups from their level-0 words v; level 2
+// also goes to lv2 for the tail.
+template <bool kFull>
+__device__ __forceinline__ void tile_levels12_pair(const uint4 (&v)[2], const mtb_layout_t &L, uint8_t *ebase,
+                                                   int y0, int x0, int K, PyrShared &sm, uint8_t *lv2) {
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int j = tid >> 4, cg = tid & 15;
     // level 1, row j, columns 8cg..8cg+7 (a pixel exists iff both its rows and
     // both its columns do, so the level-1 bounds cover the garbage of groups
     // that were not loaded)
