@@ -140,7 +140,12 @@ __device__ __forceinline__ int ld_acquire(const int32_t *p) {
 
 // Spins (thread-level) until *ctr >= target.  Gives up when *status is already
 // set by another wait, or after timeout_ns, in which case it sets *status to
-// MTB_ERR_TIMEOUT.  Returns true if the target was reached.
+// MTB_ERR_TIMEOUT.  Returns true if the target was reached.  The sleep between
+// polls grows from 32 ns to kWaitMaxSleepNs: the search's level-to-level hops
+// are a few microseconds, and a longer ceiling (1 us) made each waiter notice
+// its dependency up to that much late (4000x3000x3 one-call step: 90.0 us with
+// 1024 ns, 86.2 us with 64 ns).
+constexpr unsigned kWaitMaxSleepNs = 64;
 __device__ __forceinline__ bool wait_at_least(const int32_t *ctr, int target, int32_t *status,
                                               unsigned long long timeout_ns) {
     if (ld_acquire(ctr) >= target) return true;
@@ -148,7 +153,7 @@ __device__ __forceinline__ bool wait_at_least(const int32_t *ctr, int target, in
     unsigned ns = 32;
     for (;;) {
         __nanosleep(ns);
-        if (ns < 1024) ns <<= 1;
+        if (ns < kWaitMaxSleepNs) ns <<= 1;
         if (ld_acquire(ctr) >= target) return true;
         if (ld_acquire(status) != 0) return false;
         if (global_timer_ns() > deadline) {
