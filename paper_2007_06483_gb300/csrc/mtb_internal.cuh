@@ -34,9 +34,12 @@ constexpr int kMaxShiftThreads = 256;
 // most kBruteBudget word-candidate evaluations per pair is searched by brute
 // force over that window; the coarse-to-fine chain through those levels is
 // then walked in the resulting error tables (kTableWords per pair: the windows
-// of radius 1, 3, 7 and 15 take 9 + 49 + 225 + 961 = 1244 words).
+// of radius 1, 3, 7 and 15 take 9 + 49 + 225 + 961 = 1244 words).  2M per
+// pair: on 4000x3000 and 6000x4000 stacks the radius-15 window (961
+// candidates) costs more than one more 9-candidate hop (one-call step 86.0 ->
+// 84.9 us and 269 -> 263 us against a budget of 8M).
 constexpr int kMaxTableRadius = 15;
-constexpr long long kBruteBudget = 8ll << 20;
+constexpr long long kBruteBudget = 2ll << 20;
 constexpr int kTableWords = 1280;
 
 // Bound on any device-side wait of the search (the waits always end when the
