@@ -237,15 +237,34 @@ int mtb_batch_create(const mtb_stack_desc_t *stacks, int count, void *workspace,
  * current contents of its image buffer). */
 int mtb_batch_run(mtb_batch_t *batch, void *stream);
 
-/* Autotuner: times `reps` runs of the batch for each candidate tile shape (runs
- * of pyramid tiles per CTA, words per bitmap chunk, search chunks per level),
- * coordinate by coordinate, and keeps the fastest.  Synchronous. */
+/* Autotuner: times `reps` runs of the batch for each candidate setting and
+ * keeps the fastest, coordinate by coordinate:
+ *   - runs of pyramid tiles per CTA: 1, 2, 4;
+ *   - words per bitmap chunk: 512, 1024, 2048, 4096;
+ *   - search chunks per level: 1, 2, 4;
+ *   - the coarse-window budget: 0, 256 or 2048 units of 1024 word-candidates
+ *     per pair.
+ * The window budget trades the brute-force windows of the coarse levels
+ * (Sec. III-B's search, counted for every candidate of the reachable window at
+ * once) against one 9-candidate hop per level; results are the same either
+ * way.  Synchronous. */
 int mtb_batch_tune(mtb_batch_t *batch, int reps, void *stream);
 
-/* The batch's tile shapes: values[0] pyramid runs per CTA, values[1] words per
- * bitmap chunk, values[2] search chunks per level (x CTAs / stacks), values[3]
- * 1 if the launch is a CUDA graph.  n_values >= 4. */
+/* The batch's settings:
+ *   - values[0]: pyramid runs per CTA;
+ *   - values[1]: words per bitmap chunk;
+ *   - values[2]: search chunks per level (x CTAs / stacks);
+ *   - values[3]: 1 if the launch is a CUDA graph;
+ *   - values[4] (written if n_values >= 5): the coarse-window budget in units
+ *     of 1024 word-candidates per pair.
+ * n_values >= 4. */
 int mtb_batch_config(const mtb_batch_t *batch, int *values, int n_values);
+
+/* Sets the batch's settings in the layout of mtb_batch_config.  values[3] is
+ * ignored.  Each other value must be one of the autotuner's candidates
+ * (MTB_ERR_INVALID_ARG otherwise).  n_values >= 5.  Replans the batch and
+ * recaptures its graph; on an error the previous settings stay. */
+int mtb_batch_set_config(mtb_batch_t *batch, const int *values, int n_values);
 
 /* Waits for `stream`, then returns MTB_OK or the first stack's non-zero status
  * word (MTB_ERR_TIMEOUT if a bounded device wait gave up). */

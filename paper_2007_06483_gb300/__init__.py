@@ -124,6 +124,7 @@ def lib():
             "mtb_batch_run": (I, [P, P]),
             "mtb_batch_tune": (I, [P, I, P]),
             "mtb_batch_config": (I, [P, ctypes.POINTER(ctypes.c_int), I]),
+            "mtb_batch_set_config": (I, [P, ctypes.POINTER(ctypes.c_int), I]),
             "mtb_batch_status": (I, [P, P]),
             "mtb_batch_destroy": (None, [P]),
             "mtb_apply_shifts": (I, [P, I, I, I, P, I, P, P]),
@@ -458,9 +459,15 @@ class Batch:
         _check(lib().mtb_batch_tune(self._h, reps, _stream(stream)), "mtb_batch_tune")
 
     def config(self) -> dict:
-        v = (ctypes.c_int * 4)()
-        _check(lib().mtb_batch_config(self._h, v, 4), "mtb_batch_config")
-        return {"pyr_runs_per_cta": v[0], "bit_chunk_words": v[1], "search_waves": v[2], "graph": bool(v[3])}
+        v = (ctypes.c_int * 5)()
+        _check(lib().mtb_batch_config(self._h, v, 5), "mtb_batch_config")
+        return {"pyr_runs_per_cta": v[0], "bit_chunk_words": v[1], "search_waves": v[2], "graph": bool(v[3]),
+                "window_kwords": v[4]}
+
+    def set_config(self, pyr_runs_per_cta: int, bit_chunk_words: int, search_waves: int, window_kwords: int):
+        """mtb_batch_set_config: pins the settings (each one of the autotuner's candidates)."""
+        v = (ctypes.c_int * 5)(pyr_runs_per_cta, bit_chunk_words, search_waves, 0, window_kwords)
+        _check(lib().mtb_batch_set_config(self._h, v, 5), "mtb_batch_set_config")
 
     def status(self, stream=None) -> int:
         return int(lib().mtb_batch_status(self._h, _stream(stream)))

@@ -311,8 +311,22 @@ struct EngineTuning {
     int pyr_runs_per_cta;  // PYR items per CTA of the launch (tiles per item follow from it)
     int bit_chunk_words;   // words per bitmap chunk
     int search_waves;      // search chunks per larger level: about search_waves * CTAs / stacks
+    int window_kwords;     // coarse-window budget, 1024 word-candidates per pair (0: no windows)
 };
-constexpr EngineTuning kDefaultTuning = {1, 1024, 1};
+constexpr EngineTuning kDefaultTuning = {1, 1024, 1, (int)(kBruteBudget >> 10)};
+// The autotuner's candidates, which mtb_batch_set_config also accepts.  Many
+// stacks in flight favour fewer coarse windows than one stack alone: their
+// 9-candidate hops overlap each other's work.
+constexpr int kRunsCand[] = {1, 2, 4};
+constexpr int kWordsCand[] = {512, 1024, 2048, 4096};
+constexpr int kWavesCand[] = {1, 2, 4};
+constexpr int kWindowCand[] = {0, 256, 2048};
+template <int N>
+bool one_of(int v, const int (&c)[N]) {
+    for (int k = 0; k < N; ++k)
+        if (v == c[k]) return true;
+    return false;
+}
 
 // Fills the item plan of one stack.  total_tiles: pyramid tiles of the whole
 // launch (all stacks), n_stacks: stacks in the launch.
@@ -340,7 +354,8 @@ int plan_stack(const mtb_layout_t &L, const uint8_t *images, uint8_t *ws, int to
     d->bit_l0_items = bitmap_chunks(L, 0, d->bit_chunk_words);
     long long search_cap = cap * (tun.search_waves > 0 ? tun.search_waves : 1) / (n_stacks > 0 ? n_stacks : 1);
     if (search_cap < 1) search_cap = 1;
-    plan_search(L, ref, search_cap, shifts_out, level_errs_out, level_shifts_out, timeout_ns, -1, &d->sp);
+    plan_search(L, ref, search_cap, shifts_out, level_errs_out, level_shifts_out, timeout_ns, -1, &d->sp, 0,
+                (long long)tun.window_kwords << 10);
     if (d->sp.total_items < 0) return MTB_ERR_INVALID_ARG;
     d->sp.bit_chunk_words = d->bit_chunk_words;
     const SearchPlan &P = d->sp;
@@ -576,19 +591,19 @@ int mtb_batch_tune(mtb_batch_t *b, int reps, void *stream) {
         cudaEventElapsedTime(ms, e0, e1);
         return rc;
     };
-    // coordinate descent over the three tile-shape knobs
-    static const int runs_c[] = {1, 2, 4};
-    static const int words_c[] = {512, 1024, 2048, 4096};
-    static const int waves_c[] = {1, 2, 4};
+    // coordinate descent over the four knobs
     EngineTuning best = b->tuning;
     float best_ms = 0;
     int rc = time_config(&best_ms);
-    for (int knob = 0; knob < 3 && rc == MTB_OK; ++knob) {
-        const int *cand = knob == 0 ? runs_c : (knob == 1 ? words_c : waves_c);
+    for (int knob = 0; knob < 4 && rc == MTB_OK; ++knob) {
+        const int *cand = knob == 0 ? kRunsCand : knob == 1 ? kWordsCand : knob == 2 ? kWavesCand : kWindowCand;
         const int nc = knob == 1 ? 4 : 3;
         for (int c = 0; c < nc && rc == MTB_OK; ++c) {
             EngineTuning t = best;
-            int &field = knob == 0 ? t.pyr_runs_per_cta : (knob == 1 ? t.bit_chunk_words : t.search_waves);
+            int &field = knob == 0   ? t.pyr_runs_per_cta
+                         : knob == 1 ? t.bit_chunk_words
+                         : knob == 2 ? t.search_waves
+                                     : t.window_kwords;
             if (field == cand[c]) continue;
             field = cand[c];
             b->tuning = t;
@@ -613,7 +628,23 @@ int mtb_batch_config(const mtb_batch_t *b, int *values, int n_values) {
     values[1] = b->tuning.bit_chunk_words;
     values[2] = b->tuning.search_waves;
     values[3] = b->graph != nullptr;
+    if (n_values >= 5) values[4] = b->tuning.window_kwords;
     return MTB_OK;
+}
+
+int mtb_batch_set_config(mtb_batch_t *b, const int *values, int n_values) {
+    if (!b || !values || n_values < 5) return MTB_ERR_INVALID_ARG;
+    if (!one_of(values[0], kRunsCand) || !one_of(values[1], kWordsCand) || !one_of(values[2], kWavesCand) ||
+        !one_of(values[4], kWindowCand))
+        return MTB_ERR_INVALID_ARG;
+    const EngineTuning old = b->tuning;
+    b->tuning = EngineTuning{values[0], values[1], values[2], values[4]};
+    const int rc = batch_build(b);
+    if (rc != MTB_OK) {
+        b->tuning = old;
+        batch_build(b);
+    }
+    return rc;
 }
 
 int mtb_batch_status(mtb_batch_t *b, void *stream) {

@@ -119,7 +119,8 @@ cudaError_t launch_gather_quadrants(const uint8_t *images, int n, int w, int h, 
                                     cudaStream_t s);
 cudaError_t launch_quadrant_flags(const int32_t *quad, int n, int rot_tol, int32_t *out, int32_t *flags,
                                   cudaStream_t s);
-int coarse_start_level(const mtb_layout_t &L);
+// budget: word-candidate evaluations per pair allowed to the coarse windows.
+int coarse_start_level(const mtb_layout_t &L, long long budget = kBruteBudget);
 // `overlap` (only directly after launch_bitmaps of the same call, on a workspace
 // the same call's launch_pyramid cleared): the search starts while the bitmaps
 // are being packed and waits per bit plane.  `chain`: each exposure is searched

@@ -94,14 +94,14 @@ int g_search_blocks_per_sm[2] = {0, 0};
 }  // namespace
 
 // Levels at or above lc are searched by whole windows (see kBruteBudget).
-int coarse_start_level(const mtb_layout_t &L) {
+int coarse_start_level(const mtb_layout_t &L, long long budget) {
     int lc = L.levels;
     while (lc > 0) {
         const int l = lc - 1;
         const long long R = (1ll << (L.levels - l)) - 1;
         if (R > kMaxTableRadius) break;
         const long long words = (long long)L.bits_pitch[l] * L.height[l];
-        if (words * (2 * R + 1) * (2 * R + 1) > kBruteBudget) break;
+        if (words * (2 * R + 1) * (2 * R + 1) > budget) break;
         --lc;
     }
     return lc;
@@ -109,13 +109,13 @@ int coarse_start_level(const mtb_layout_t &L) {
 
 void plan_search(const mtb_layout_t &L, int ref_idx, long long cap, int32_t *shifts_out, uint32_t *level_errs_out,
                  int32_t *level_shifts_out, unsigned long long timeout_ns, int withhold_pair, SearchPlan *out,
-                 int chain) {
+                 int chain, long long brute_budget) {
     SearchPlan &P = *out;
     P = SearchPlan{};
     P.ref = ref_idx;
     P.chain = chain;
     P.pairs = L.n - 1;
-    P.lc = coarse_start_level(L);
+    P.lc = coarse_start_level(L, brute_budget);
     P.shifts_out = shifts_out;
     P.level_errs_out = level_errs_out;
     P.level_shifts_out = level_shifts_out;

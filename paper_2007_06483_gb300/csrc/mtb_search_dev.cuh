@@ -22,9 +22,11 @@ struct SearchPlan {
     int first_item[MTB_MAX_LEVELS];  // queue index of pair 0, chunk 0 of level l (l < lc)
 };
 
+// brute_budget: word-candidate evaluations per pair allowed to the coarse
+// windows (0: every level is a 9-candidate hop).
 void plan_search(const mtb_layout_t &L, int ref_idx, long long cap, int32_t *shifts_out, uint32_t *level_errs_out,
                  int32_t *level_shifts_out, unsigned long long timeout_ns, int withhold_pair, SearchPlan *out,
-                 int chain = 0);
+                 int chain = 0, long long brute_budget = kBruteBudget);
 
 namespace {
 

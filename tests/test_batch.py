@@ -69,12 +69,48 @@ def test_batch_autotuner_keeps_results(mtb_lib):
     batch.tune(reps=2)
     cfg = batch.config()
     assert cfg["pyr_runs_per_cta"] in (1, 2, 4) and cfg["bit_chunk_words"] in (512, 1024, 2048, 4096)
+    assert cfg["search_waves"] in (1, 2, 4) and cfg["window_kwords"] in (0, 256, 2048)
     for s in batch.shifts:
         s.fill_(-1)
     batch.run()
     torch.cuda.synchronize()
     for a, b in zip(before, batch.shifts):
         assert torch.equal(a, b)
+    batch.close()
+
+
+def test_batch_set_config_rejects_invalid_arguments_on_host(mtb_lib):
+    v = (ctypes.c_int * 5)(1, 1024, 1, 0, 2048)
+    assert mtb_lib.lib().mtb_batch_set_config(None, v, 5) == mtb_lib.MTB_ERR_INVALID_ARG
+    assert mtb_lib.lib().mtb_batch_config(None, v, 5) == mtb_lib.MTB_ERR_INVALID_ARG
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("cfg", [(1, 1024, 1, 0), (2, 512, 4, 256), (4, 4096, 2, 2048), (1, 2048, 1, 0)])
+def test_batch_every_setting_matches_plain_path(mtb_lib, cfg):
+    """The coarse-window budget moves levels between brute-force windows and
+    9-candidate hops (0: none windowed); the other settings change item sizes.
+    Every setting must give the plain path's shifts, errors and level shifts."""
+    stacks = _stacks()
+    batch = mtb_lib.Batch(stacks)
+    batch.set_config(*cfg)
+    got = batch.config()
+    assert (got["pyr_runs_per_cta"], got["bit_chunk_words"], got["search_waves"], got["window_kwords"]) == cfg
+    assert got["graph"]
+    for attempt in range(2):
+        batch.run()
+        torch.cuda.synchronize()
+        assert batch.status() == mtb_lib.MTB_OK
+        for k, st in enumerate(stacks):
+            ps, pe, pl = mtb_lib.align_stack(st["images"], st["levels"], 4, st["ref_idx"], level_outputs=True)
+            assert torch.equal(ps, batch.shifts[k]), (cfg, k)
+            assert torch.equal(pe, batch.level_errs[k]), (cfg, k)
+            assert torch.equal(pl, batch.level_shifts[k]), (cfg, k)
+    with pytest.raises(mtb_lib.MtbError):
+        batch.set_config(1, 1024, 1, 100)  # not one of the candidates
+    with pytest.raises(mtb_lib.MtbError):
+        batch.set_config(3, 1024, 1, 0)
+    assert batch.config() == got
     batch.close()
 
 
