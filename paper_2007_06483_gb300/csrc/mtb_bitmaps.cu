@@ -29,7 +29,9 @@ namespace {
 // CTAs are numbered deep levels first, then the tile levels from the coarsest
 // to level 0, each over all exposures: the planes a chained search needs first
 // (its coarse levels) are finished first.
-__global__ void __launch_bounds__(kBitThreads)
+// 5 CTAs per SM (48 registers, no spills): 17.0 us for the 4000x3000x3 planes
+// and 59.9 us for 6000x4000x7, against 18.9 and 70.4 us at 4 (54 registers).
+__global__ void __launch_bounds__(kBitThreads, 5)
 k_bitmaps(const mtb_layout_t L, uint8_t *__restrict__ ws, int tol, int deep_ctas) {
     __shared__ uint32_t s_hist[256];
     __shared__ int s_med;
