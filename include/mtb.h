@@ -167,6 +167,17 @@ int mtb_search_shifts(int n_exposures, int w, int h, int levels, int ref_idx,
                       void *workspace, size_t workspace_bytes, int32_t *shifts_out,
                       uint32_t *level_errs_out, int32_t *level_shifts_out, void *stream);
 
+/* Status of the device-side work of the last search enqueued on `stream` (by
+ * any entry point that runs the shift search on a stream; batches report
+ * through mtb_batch_status): MTB_OK, or MTB_ERR_TIMEOUT if a bounded
+ * device-side wait gave up.  Waits for `stream` first.  MTB_OK if no search
+ * was ever enqueued on `stream`; MTB_ERR_CUDA if the wait fails.  Unlike
+ * mtb_workspace_status it needs no workspace, so it also serves calls whose
+ * workspace the library allocated and has freed.  The library keeps the
+ * status of the 256 most recent streams per device in a static device array;
+ * it allocates nothing. */
+int mtb_get_last_status(void *stream);
+
 /* Status word of the last search run in `workspace` (sizes as when it ran):
  * MTB_OK, or MTB_ERR_TIMEOUT if a bounded device-side wait gave up.  Waits for
  * `stream` first, then copies 4 bytes to the host.  Device-side waits only end

@@ -123,6 +123,7 @@ def lib():
             "mtb_batch_create": (I, [P, I, P, S, ctypes.POINTER(ctypes.c_void_p)]),
             "mtb_batch_run": (I, [P, P]),
             "mtb_batch_tune": (I, [P, I, P]),
+            "mtb_get_last_status": (I, [P]),
             "mtb_batch_config": (I, [P, ctypes.POINTER(ctypes.c_int), I]),
             "mtb_batch_set_config": (I, [P, ctypes.POINTER(ctypes.c_int), I]),
             "mtb_batch_status": (I, [P, P]),
@@ -300,6 +301,12 @@ def workspace_status(workspace, n: int, w: int, h: int, levels: int, stream=None
     """Status word of the last search in `workspace` (MTB_OK or MTB_ERR_TIMEOUT)."""
     return int(lib().mtb_workspace_status(workspace.data_ptr(), workspace.numel(), n, w, h, levels,
                                           _stream(stream)))
+
+
+def get_last_status(stream=None) -> int:
+    """mtb_get_last_status: MTB_OK or MTB_ERR_TIMEOUT for the last search enqueued
+    on `stream` (torch stream or None for the current one); waits for it."""
+    return int(lib().mtb_get_last_status(_stream(stream)))
 
 
 def align_stack_host(images, levels: int, noise_tol: int = 4, ref_idx: int = 0, *, device_workspace=None,

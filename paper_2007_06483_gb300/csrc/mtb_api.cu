@@ -247,6 +247,16 @@ const char *mtb_status_string(int status) {
 
 int mtb_abi_version(void) { return 1; }
 
+int mtb_get_last_status(void *stream) {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return MTB_ERR_CUDA;
+    const int slot = last_status_slot(s, false);
+    if (slot < 0) return MTB_OK;  // no search was ever launched on this stream
+    int32_t v = MTB_OK;
+    if (read_last_status(slot, &v) != MTB_OK) return MTB_ERR_CUDA;
+    return v;
+}
+
 size_t mtb_workspace_bytes(int n_exposures, int w, int h, int levels) {
     mtb_layout_t L;
     if (compute_layout(n_exposures, w, h, levels, &L) != MTB_OK) return 0;

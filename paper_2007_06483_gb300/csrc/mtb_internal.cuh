@@ -121,6 +121,11 @@ cudaError_t launch_quadrant_flags(const int32_t *quad, int n, int rot_tol, int32
                                   cudaStream_t s);
 // budget: word-candidate evaluations per pair allowed to the coarse windows.
 int coarse_start_level(const mtb_layout_t &L, long long budget = kBruteBudget);
+// Stream s's last-status slot on the current device: its index (-1 if there is
+// none, or none may be taken without `create`) and, in *dev_slot, its device
+// address.  read_last_status copies a slot's value to the host (synchronous).
+int last_status_slot(cudaStream_t s, bool create, int32_t **dev_slot = nullptr);
+int read_last_status(int slot, int32_t *out);
 // `overlap` (only directly after launch_bitmaps of the same call, on a workspace
 // the same call's launch_pyramid cleared): the search starts while the bitmaps
 // are being packed and waits per bit plane.  `chain`: each exposure is searched

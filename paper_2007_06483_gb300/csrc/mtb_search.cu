@@ -30,7 +30,11 @@
 // CTAs take items in queue order, so every item waits only on items taken
 // earlier by running CTAs: the waits always end.  Each wait is still bounded
 // by a timeout that sets the workspace status word instead of hanging.
+#include <mutex>
+
 #include "mtb_search_dev.cuh"
+
+static __device__ int32_t g_last_status[256];  // see last_status_slot
 
 namespace mtb {
 namespace {
@@ -91,7 +95,57 @@ __global__ void k_clear_search(const mtb_layout_t L, uint8_t *__restrict__ ws, i
 
 int g_search_blocks_per_sm[2] = {0, 0};
 
+// Last-status slots: one int32 per (device, stream) in a static device array,
+// written by the final item of every search launched on the stream.  The
+// runtime creates the array with the module: taking a slot allocates nothing.
+constexpr int kStatusSlots = 256;
+struct StatusSlots {
+    int32_t *dev = nullptr;  // g_last_status on this device
+    cudaStream_t key[kStatusSlots] = {};
+    bool used[kStatusSlots] = {};
+    int next = 0;  // slot to take when all are used (oldest first)
+};
+StatusSlots g_status[64];
+std::mutex g_status_mu;
+
 }  // namespace
+
+int last_status_slot(cudaStream_t s, bool create, int32_t **dev_slot) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return -1;
+    std::lock_guard<std::mutex> g(g_status_mu);
+    StatusSlots &t = g_status[dev];
+    if (!t.dev) {
+        void *a = nullptr;
+        if (cudaGetSymbolAddress(&a, g_last_status) != cudaSuccess) {
+            cudaGetLastError();
+            return -1;
+        }
+        t.dev = static_cast<int32_t *>(a);
+    }
+    int k = 0;
+    while (k < kStatusSlots && !(t.used[k] && t.key[k] == s)) ++k;
+    if (k == kStatusSlots) {
+        if (!create) return -1;
+        k = 0;
+        while (k < kStatusSlots && t.used[k]) ++k;
+        if (k == kStatusSlots) {  // every slot taken: reuse the oldest
+            k = t.next;
+            t.next = (t.next + 1) % kStatusSlots;
+        }
+        t.used[k] = true;
+        t.key[k] = s;
+    }
+    if (dev_slot) *dev_slot = t.dev + k;
+    return k;
+}
+
+int read_last_status(int slot, int32_t *out) {
+    return cudaMemcpyFromSymbol(out, g_last_status, sizeof(int32_t), (size_t)slot * sizeof(int32_t),
+                                cudaMemcpyDeviceToHost) == cudaSuccess
+               ? MTB_OK
+               : MTB_ERR_CUDA;
+}
 
 // Levels at or above lc are searched by whole windows (see kBruteBudget).
 int coarse_start_level(const mtb_layout_t &L, long long budget) {
@@ -170,6 +224,8 @@ cudaError_t launch_search_ex(const mtb_layout_t &L, int ref_idx, uint8_t *ws, in
     plan_search(L, ref_idx, cap, shifts_out, level_errs_out, level_shifts_out, timeout_ns, withhold_pair, &P,
                 chain ? 1 : 0);
     if (P.total_items < 0) return cudaErrorInvalidValue;
+    P.status_out = nullptr;
+    last_status_slot(s, true, &P.status_out);
     const int grid = (int)(P.total_items < cap ? P.total_items : cap);
     if (overlap)  // the pyramid stage of the same call cleared the search's areas
         return launch_k(k_search<true>, dim3(grid), dim3(kSearchThreads), s, true, L, ws, P);

@@ -16,6 +16,7 @@ struct SearchPlan {
     int32_t *level_shifts_out;
     unsigned long long timeout_ns;
     int withhold_pair;  // test hook: this pair's resolve item never reports completion (-1: none)
+    int32_t *status_out;  // the launching stream's last-status slot (host-mapped; may be null)
     int tx[MTB_MAX_LEVELS], ty[MTB_MAX_LEVELS], col_blocks[MTB_MAX_LEVELS], chunks[MTB_MAX_LEVELS];
     int rows_per_thread[MTB_MAX_LEVELS];
     int bit_chunk_words;  // words per bitmap chunk (the engine waits for all chunks of a level)
@@ -431,6 +432,8 @@ __device__ void shift_item(const mtb_layout_t &L, uint8_t *ws, const SearchPlan 
 }
 
 // Final item: waits for level 0 of every pair, then writes the outputs.
+// Every way out of it leaves the search's status word (MTB_OK or
+// MTB_ERR_TIMEOUT) in the stream's last-status slot.
 __device__ void final_item(const mtb_layout_t &L, uint8_t *ws, const SearchPlan &P, SearchShared &sm) {
     if (threadIdx.x == 0) {
         int ok = 1;
@@ -438,6 +441,12 @@ __device__ void final_item(const mtb_layout_t &L, uint8_t *ws, const SearchPlan 
             ok = wait_at_least(done_ctr(ws, L, p, 0), level_target(P, 0), status_word(ws, L), P.timeout_ns);
         sm.ok = ok;
         __threadfence();
+        if (P.status_out) {
+            // the other items' waits that gave up have set the word by now or
+            // set it after this one: a timeout is seen here or by ok == 0
+            const int st = ld_acquire(status_word(ws, L));
+            *reinterpret_cast<volatile int32_t *>(P.status_out) = st != 0 ? st : (ok ? MTB_OK : MTB_ERR_TIMEOUT);
+        }
     }
     __syncthreads();
     if (!sm.ok) return;

@@ -158,7 +158,32 @@ def test_bounded_wait_reports_timeout(mtb_lib):
     rc = mtb_lib.lib().mtb_debug_search_withheld(n, w, h, L, spec.ref, ws.data_ptr(), ws.numel(), 2_000_000, stream)
     assert rc == mtb_lib.MTB_ERR_TIMEOUT
     assert mtb_lib.workspace_status(ws, n, w, h, L) == mtb_lib.MTB_ERR_TIMEOUT
+    assert mtb_lib.get_last_status() == mtb_lib.MTB_ERR_TIMEOUT  # the stream's slot: no workspace needed
     shifts = torch.empty((n, 2), dtype=torch.int32, device="cuda")
     mtb_lib.search_shifts(n, w, h, L, spec.ref, ws, shifts)
     assert mtb_lib.workspace_status(ws, n, w, h, L) == mtb_lib.MTB_OK
+    assert mtb_lib.get_last_status() == mtb_lib.MTB_OK
     assert np.array_equal(shifts.cpu().numpy(), synth.expected_shifts(spec))
+
+
+@pytest.mark.gpu
+def test_last_status_per_stream(mtb_lib):
+    """Each stream keeps the status of its own last search; a stream that never
+    ran one reports MTB_OK; a call whose workspace the library allocated and
+    freed still reports through its stream."""
+    spec = synth.small_spec(78, 320, 240, n=3, levels=5, shift_range=5, ref=1)
+    imgs = synth.make_stack(spec, "cuda")
+    torch.cuda.synchronize()  # the images come from the current stream; the test uses others
+    n, w, h, L = spec.n, spec.w, spec.h, spec.levels
+    s1, s2, s3 = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    assert mtb_lib.get_last_status(s3) == mtb_lib.MTB_OK
+    ws = mtb_lib.new_workspace(n, w, h, L)
+    mtb_lib.build_pyramids(imgs, L, ws, stream=s1)
+    mtb_lib.build_bitmaps(n, w, h, L, spec.noise_tol, ws, stream=s1)
+    rc = mtb_lib.lib().mtb_debug_search_withheld(n, w, h, L, spec.ref, ws.data_ptr(), ws.numel(), 2_000_000,
+                                                 s1.cuda_stream)
+    assert rc == mtb_lib.MTB_ERR_TIMEOUT
+    out = mtb_lib.align_stack(imgs, L, spec.noise_tol, spec.ref, stream=s2)  # workspace allocated and freed
+    assert mtb_lib.get_last_status(s2) == mtb_lib.MTB_OK
+    assert mtb_lib.get_last_status(s1) == mtb_lib.MTB_ERR_TIMEOUT
+    assert np.array_equal(out.cpu().numpy(), synth.expected_shifts(spec))
