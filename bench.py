@@ -60,10 +60,10 @@ FALLBACK_HBM_GBS = 6800.0
 # sources at capture time; reported only while those sources are unchanged.
 NCU_TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum (cold cache), one
-    # launch each: k_pyramid of the 4000x3000x3 stack (109.69 MB read + 6.93 MB
-    # written) and k_apply_shifts of the 6000x4000x7 stack (496.84 + 458.71 MB)
-    ("k_pyramid", "stack4000x3000x3"): {"bytes": 116623104, "sources_sha256": "db1fded4799b174e92edf848db2e9500d7b8e542b3d217acde503943385d2968"},
-    ("k_apply_shifts", "apply6000x4000x7"): {"bytes": 955552256, "sources_sha256": "40536e741a1378bde169320db4c200f28e2922bc0e77e2b9c23f2d8cca0bbc17"},
+    # launch each: k_pyramid of the 4000x3000x3 stack (109.69 MB read + 6.94 MB
+    # written) and k_apply_shifts of the 6000x4000x7 stack (496.81 + 459.04 MB)
+    ("k_pyramid", "stack4000x3000x3"): {"bytes": 116625920, "sources_sha256": "15766a868c4262128ec6da015fac0538d7a4e082a5b300a221866e1585317d14"},
+    ("k_apply_shifts", "apply6000x4000x7"): {"bytes": 955854592, "sources_sha256": "3871dbf63060dbcd338d34f28c0872d4b6ad92193a22b4e265c63c63061831c1"},
 }
 
 
