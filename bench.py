@@ -60,10 +60,10 @@ FALLBACK_HBM_GBS = 6800.0
 # sources at capture time; reported only while those sources are unchanged.
 NCU_TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum (cold cache), one
-    # launch each: k_pyramid of the 4000x3000x3 stack (109.69 MB read + 6.94 MB
-    # written) and k_apply_shifts of the 6000x4000x7 stack (496.81 + 459.04 MB)
-    ("k_pyramid", "stack4000x3000x3"): {"bytes": 116625920, "sources_sha256": "15766a868c4262128ec6da015fac0538d7a4e082a5b300a221866e1585317d14"},
-    ("k_apply_shifts", "apply6000x4000x7"): {"bytes": 955854592, "sources_sha256": "3871dbf63060dbcd338d34f28c0872d4b6ad92193a22b4e265c63c63061831c1"},
+    # launch each: k_pyramid of the 4000x3000x3 stack (109.71 MB read + 6.95 MB
+    # written) and k_apply_shifts of the 6000x4000x7 stack (496.80 + 458.93 MB)
+    ("k_pyramid", "stack4000x3000x3"): {"bytes": 116654080, "sources_sha256": "c6c43bafd4b5358404d2793248d824c31c83ae701c9e99a30a98a092789c0be0"},
+    ("k_apply_shifts", "apply6000x4000x7"): {"bytes": 955731456, "sources_sha256": "ed1522d46c65b2bbdc20016da0219b14ed12bac42d4992afea0df26c0aa84b95"},
 }
 
 
