@@ -8,7 +8,10 @@ which starts while the bitmaps are still being packed), chained by
 programmatic dependent launch.  The
 default workload is the 4000x3000 stack of 3 exposures (2 pairs, 7 levels).
 The metric is aligned MPix/s: full-resolution pixels of every aligned pair
-divided by the step time.  A second loop of the same length times the same work
+divided by the step time.  The K timed steps run back to back between two
+events: an event between two steps would serialise one step's search with the
+next step's launches.  p50/p99 latency comes from a second loop with events
+around each step.  A third loop of the same length times the same work
 through the three stage calls (mtb_build_pyramids, mtb_build_bitmaps,
 mtb_search_shifts) with CUDA events between them on the launching stream: the
 split by stage, and the duration of the dominant kernel (k_pyramid) for the
@@ -60,9 +63,9 @@ FALLBACK_HBM_GBS = 6800.0
 # sources at capture time; reported only while those sources are unchanged.
 NCU_TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum (cold cache), one
-    # launch each: k_pyramid of the 4000x3000x3 stack (109.71 MB read + 6.95 MB
+    # launch each: k_pyramid of the 4000x3000x3 stack (109.70 MB read + 7.11 MB
     # written) and k_apply_shifts of the 6000x4000x7 stack (496.80 + 458.93 MB)
-    ("k_pyramid", "stack4000x3000x3"): {"bytes": 116654080, "sources_sha256": "c6c43bafd4b5358404d2793248d824c31c83ae701c9e99a30a98a092789c0be0"},
+    ("k_pyramid", "stack4000x3000x3"): {"bytes": 116816128, "sources_sha256": "e191e31d72a0aea9d54bbbc8e7e76c019b4b8616356a3e6b3adf76d31d95c4fc"},
     ("k_apply_shifts", "apply6000x4000x7"): {"bytes": 955731456, "sources_sha256": "ed1522d46c65b2bbdc20016da0219b14ed12bac42d4992afea0df26c0aa84b95"},
 }
 
@@ -301,24 +304,33 @@ def run_gb300(args):
         step(k % B)
     torch.cuda.synchronize(dev)
 
+    # throughput: K steps back to back between two events (an event between
+    # two steps would end the overlap of one step's search with the next
+    # step's launches)
     K = args.steps
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(K)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     sampler = ClockSampler(dev.index if dev.index is not None else 0)
     sampler.start()
     barrier(world)
     torch.cuda.synchronize(dev)
     t_wall = time.perf_counter()
+    t0.record(stream)
     for k in range(K):
-        step(k % B, evs[k])
+        step(k % B)
+    t1.record(stream)
     torch.cuda.synchronize(dev)
     t_wall = time.perf_counter() - t_wall
     barrier(world)
     clocks = sampler.stop()
-
-    total_ms = evs[0][0].elapsed_time(evs[-1][1])
-    step_ms = [e[0].elapsed_time(e[1]) for e in evs]
-    total_ms = max_over_ranks(total_ms, world, dev)
+    total_ms = max_over_ranks(t0.elapsed_time(t1), world, dev)
     ms_per_step = total_ms / K
+
+    # latency: the same steps, each between its own two events
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(K)]
+    for k in range(K):
+        step(k % B, evs[k])
+    torch.cuda.synchronize(dev)
+    step_ms = [e[0].elapsed_time(e[1]) for e in evs]
 
     # the same work through the three stage calls, for the split by stage
     sev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(max(3, K))]

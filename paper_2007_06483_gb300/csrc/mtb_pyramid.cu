@@ -154,10 +154,14 @@ k_pyramid(const uint8_t *__restrict__ images, const mtb_layout_t L, uint8_t *__r
     else pyramid_general(images, L, ws, tiles_x, tiles_per_exp, t0, t1, sm);
 }
 
-// Clears n 32-bit words (the histograms and counters of a stack).
-// The pyramid pass chained after it may start at once: it writes only gray
-// planes before its griddepcontrol.wait, and nothing this kernel clears.
+// Clears n 32-bit words (the histograms and counters of a stack).  Launched
+// chained behind whatever the stream ran before (usually the previous call's
+// search), so its launch overlaps that kernel's end; it waits for it before
+// it lets the pyramid pass start, because the pyramid pass writes gray planes
+// that the previous call's bitmap pass may still read.  The pyramid pass in
+// turn writes only gray planes, nothing cleared here, before its own wait.
 __global__ void k_clear(uint32_t *p, int n) {
+    pdl_wait();
     pdl_trigger();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = 0;
 }
@@ -175,7 +179,7 @@ cudaError_t launch_clear_stack(const mtb_layout_t &L, uint8_t *ws, cudaStream_t 
     const long long cap = 4ll * device_sm_count();
     const long long blocks = (words + 1023) / 1024 < cap ? (words + 1023) / 1024 : cap;
     if (words > 0x7fffffffLL) return cudaErrorInvalidValue;
-    return launch_k(k_clear, dim3((unsigned)blocks), dim3(256), s, false,
+    return launch_k(k_clear, dim3((unsigned)blocks), dim3(256), s, true,
                     reinterpret_cast<uint32_t *>(ws + L.hist_offset), (int)words);
 }
 
