@@ -10,12 +10,12 @@ default workload is the 4000x3000 stack of 3 exposures (2 pairs, 7 levels).
 The metric is aligned MPix/s: full-resolution pixels of every aligned pair
 divided by the step time.  The K timed steps run back to back between two
 events: an event between two steps would serialise one step's search with the
-next step's launches.  p50/p99 latency comes from a second loop with events
-around each step.  A third loop of the same length times the same work
-through the three stage calls (mtb_build_pyramids, mtb_build_bitmaps,
-mtb_search_shifts) with CUDA events between them on the launching stream: the
-split by stage, and the duration of the dominant kernel (k_pyramid) for the
-roofline.
+next step's launches. p50/p99 latency comes from a second loop with events
+around each step (at least 100 timed steps after 10 more warm-ups). A third
+loop of K steps times the same work through the three stage calls
+(mtb_build_pyramids, mtb_build_bitmaps, mtb_search_shifts) with CUDA events
+between them on the launching stream: the split by stage, and the duration of
+the dominant kernel (k_pyramid) for the roofline.
 
 Inputs and workspaces rotate over several device copies, so between two uses of
 one buffer more than 3x the L2 capacity is written and read: every step starts
@@ -55,6 +55,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "aligned MPix/s per exposure pair"
 UNIT = "MPix/s"
+# plain-path latency: p50/p99 over at least LAT_STEPS timed steps after
+# LAT_WARMUP untimed ones
+LAT_STEPS = 100
+LAT_WARMUP = 10
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 
@@ -234,6 +238,37 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- CPU baseline
+def host_cpu() -> dict:
+    """The host the oracle baseline ran on: online cores, cores this process may
+    use, architecture and CPU model (x86 `model name`; on Arm, where
+    /proc/cpuinfo has none, lscpu's model name or the implementer/part codes)."""
+    import platform
+
+    info = {"nproc": os.cpu_count(), "usable_cores": len(os.sched_getaffinity(0)), "arch": platform.machine(),
+            "model": None}
+    fields = {}
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k, _, v = line.partition(":")
+                fields.setdefault(k.strip(), v.strip())
+    except OSError:
+        pass
+    info["model"] = fields.get("model name") or None
+    if info["model"] is None:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.strip().startswith("Model name:"):
+                    info["model"] = line.split(":", 1)[1].strip()
+                    break
+        except (OSError, subprocess.SubprocessError):
+            pass
+    if info["model"] is None and "CPU implementer" in fields:
+        info["model"] = f"implementer {fields['CPU implementer']} part {fields.get('CPU part', '?')}"
+    return info
+
+
 def oracle_rate(images_np, spec, budget_s: float = 12.0, max_s: float = 30.0) -> dict:
     """Single-threaded oracle on the same stack, repeated to about budget_s."""
     import oracle
@@ -250,7 +285,7 @@ def oracle_rate(images_np, spec, budget_s: float = 12.0, max_s: float = 30.0) ->
     rate = spec.aligned_pixels * reps / total / 1e6
     return {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{reps} x full {spec.name} stack ({spec.pairs} pairs), single-threaded C oracle, {total:.1f} s",
-            "result": res}
+            "host": host_cpu(), "result": res}
 
 
 # ----------------------------------------------------------------------------- GPU arm
@@ -325,9 +360,13 @@ def run_gb300(args):
     total_ms = max_over_ranks(t0.elapsed_time(t1), world, dev)
     ms_per_step = total_ms / K
 
-    # latency: the same steps, each between its own two events
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(K)]
-    for k in range(K):
+    # latency: max(LAT_STEPS, K) steps, each between its own two events, after
+    # LAT_WARMUP more untimed ones
+    for k in range(LAT_WARMUP):
+        step(k % B)
+    n_lat = max(LAT_STEPS, K)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(n_lat)]
+    for k in range(n_lat):
         step(k % B, evs[k])
     torch.cuda.synchronize(dev)
     step_ms = [e[0].elapsed_time(e[1]) for e in evs]
@@ -411,8 +450,8 @@ def run_gb300(args):
                        "stacks_per_step_per_gpu": 1, "parallelism": f"replicas x{world}",
                        "l2": f"inputs+workspaces rotate over {B} device copies "
                              f"({B * (spec.input_bytes + wss[0].numel()) / 1e6:.0f} MB > L2)"},
-            "latency_ms": {"p50": round(statistics.median(step_ms), 5),
-                           "p99": round(sorted(step_ms)[min(len(step_ms) - 1, int(math.ceil(0.99 * len(step_ms))) - 1)], 5)},
+            "latency_ms": {"p50": round(_pct(step_ms, 0.50), 5), "p99": round(_pct(step_ms, 0.99), 5),
+                           "runs": len(step_ms), "warmup": LAT_WARMUP},
             "hbm_gbs": round(step_bytes / (ms_per_step / 1e3) / 1e9, 1),
             "stages": stages,
             "roofline": roofline,
@@ -471,7 +510,8 @@ def run_reference(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
         "config": {"workload": spec.name, "w": spec.w, "h": spec.h, "n_exposures": spec.n, "pairs": spec.pairs,
                    "levels": spec.levels, "noise_tol": spec.noise_tol, "ref": spec.ref},
-        "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                         "host": host_cpu()},
         "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -553,7 +593,8 @@ def run_batch(args):
         "plain_path": {"value": round(pixels / (plain_ms / 1e3) / 1e6, 2), "ms_per_step": round(plain_ms, 4),
                        "same_shifts_as_batch": bool(same)},
         "batch_vs_plain": round(plain_ms / ms, 3),
-        "latency_ms": {"p50": round(statistics.median(step_ms), 4), "p99": round(max(step_ms), 4)},
+        "latency_ms": {"p50": round(_pct(step_ms, 0.50), 4), "p99": round(_pct(step_ms, 0.99), 4),
+                       "runs": len(step_ms)},
         "hbm_gbs": round(achieved, 1),
         "roofline": {"bound": "hbm", "kernel": "k_engine<batch> (after k_engine_clear)", "achieved": round(achieved, 1),
                      "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
@@ -860,7 +901,8 @@ def run_paper(args):
                 "d2h_bytes_per_step": 7 * 8},
         "cpu_baseline": None if args.no_cpu_baseline else {
             "value": round(synth.paper_specs()[-1].aligned_pixels / (last["oracle_1core_ms"] / 1e3) / 1e6, 2),
-            "unit": UNIT, "cores": 1, "kind": "oracle", "sample": "one run per stack size, single-threaded C oracle"},
+            "unit": UNIT, "cores": 1, "kind": "oracle", "sample": "one run per stack size, single-threaded C oracle",
+            "host": host_cpu()},
         "gpu_launches": kernels_per_step(None) * K,
     }
     print(json.dumps(line), flush=True)
