@@ -36,8 +36,12 @@
  *     exposures back to back, base address 16-byte aligned.
  *   - Shifts are int32 (sx, sy) pairs: the translation to apply to exposure i so
  *     that it lines up with exposure ref_idx; the ref_idx row is (0, 0).
- *   - The caller owns every buffer it passes.  The library keeps nothing between
- *     calls except buffers it allocated and freed on the stream itself.
+ *   - The caller owns every buffer it passes.  Between calls the library keeps
+ *     only per-device state made on first use and held until the process exits
+ *     (the copy stream and events of mtb_align_stack_host, the last-status
+ *     array of mtb_get_last_status, the scratch array of
+ *     mtb_align_stack_noalloc), besides buffers it allocated and frees
+ *     stream-ordered on the caller's stream.
  *   - Return value: MTB_OK or one of the negative MTB_ERR_* codes.  Arguments are
  *     checked before anything is enqueued; an invalid call enqueues nothing.
  */
