@@ -21,7 +21,9 @@ Inputs and workspaces rotate over several device copies, so between two uses of
 one buffer more than 3x the L2 capacity is written and read: every step starts
 with its data in HBM.  `e2e` times the host-buffer entry point
 (mtb_align_stack_host) from pinned host memory: copy in, align, copy the shifts
-out.  `cpu_baseline` times the single-threaded oracle on the same stack.
+out.  `cpu_baseline` times the single-threaded oracle on the same stack;
+`cpu_baseline_threaded` runs that oracle on every usable host core at once,
+each thread aligning whole stacks (labelled with the thread count).
 
 Other workloads: `batchN` (N uneven stacks in one persistent launch, against the
 plain path), `serve` (Poisson arrivals of 6000x4000x7 jobs into the serving
@@ -67,10 +69,10 @@ FALLBACK_HBM_GBS = 6800.0
 # sources at capture time; reported only while those sources are unchanged.
 NCU_TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum (cold cache), one
-    # launch each: k_pyramid of the 4000x3000x3 stack (109.70 MB read + 7.11 MB
-    # written) and k_apply_shifts of the 6000x4000x7 stack (496.80 + 458.93 MB)
-    ("k_pyramid", "stack4000x3000x3"): {"bytes": 116816128, "sources_sha256": "e191e31d72a0aea9d54bbbc8e7e76c019b4b8616356a3e6b3adf76d31d95c4fc"},
-    ("k_apply_shifts", "apply6000x4000x7"): {"bytes": 955731456, "sources_sha256": "ed1522d46c65b2bbdc20016da0219b14ed12bac42d4992afea0df26c0aa84b95"},
+    # launch each: k_pyramid of the 4000x3000x3 stack (109.70 MB read + 7.02 MB
+    # written) and k_apply_shifts of the 6000x4000x7 stack (496.90 + 458.23 MB)
+    ("k_pyramid", "stack4000x3000x3"): {"bytes": 116722432, "sources_sha256": "cc9d865048422a90249c4f58f1fa03e3581da46f126e89acf788ede5240e2f36"},
+    ("k_apply_shifts", "apply6000x4000x7"): {"bytes": 955125760, "sources_sha256": "4b7f3ffd94b326a5d686199ec8fa8202e960c3c889570379abf50ac3b10a00c0"},
 }
 
 
@@ -83,6 +85,8 @@ def parse_args(argv=None):
     p.add_argument("--workload", default="stack4000x3000x3")
     p.add_argument("--buffers", type=int, default=4, help="device copies rotated over the steps")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-threads", type=int, default=0,
+                   help="threads of the threaded oracle baseline (0: the usable cores; 1: skip it)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--rates", default="10,30,100,300,1000,2000", help="serve: offered jobs/s")
     p.add_argument("--pool", type=int, default=32, help="serve: distinct pre-generated jobs")
@@ -288,6 +292,40 @@ def oracle_rate(images_np, spec, budget_s: float = 12.0, max_s: float = 30.0) ->
             "host": host_cpu(), "result": res}
 
 
+def oracle_rate_threaded(images_np, spec, threads: int, budget_s: float = 8.0) -> dict:
+    """The same oracle on `threads` host threads at once, each aligning the whole
+    stack again and again for about budget_s (the C oracle is reentrant and its
+    calls release the GIL).  A reported baseline only, labelled with the thread
+    count; the time runs until the last thread's last stack is done."""
+    import threading
+
+    import oracle
+
+    oracle.align_stack(images_np, spec.levels, spec.noise_tol, spec.ref)  # library loaded
+    done = [0] * threads
+    t0 = time.perf_counter()
+    stop = t0 + budget_s
+
+    def work(i):
+        while True:
+            oracle.align_stack(images_np, spec.levels, spec.noise_tol, spec.ref)
+            done[i] += 1
+            if time.perf_counter() >= stop:
+                return
+
+    pool = [threading.Thread(target=work, args=(i,)) for i in range(threads)]
+    for t in pool:
+        t.start()
+    for t in pool:
+        t.join()
+    total = time.perf_counter() - t0
+    stacks = sum(done)
+    return {"value": round(spec.aligned_pixels * stacks / total / 1e6, 3), "unit": UNIT, "cores": threads,
+            "kind": "oracle", "sample": f"{stacks} x full {spec.name} stack on {threads} threads (each thread "
+                                        f"aligns whole stacks), single-threaded C oracle per thread, {total:.1f} s",
+            "host": host_cpu()}
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def run_gb300(args):
     import numpy as np
@@ -432,13 +470,16 @@ def run_gb300(args):
                "ms_per_step": round(e_ms, 4), "h2d_bytes_per_step": int(host.numel()),
                "d2h_bytes_per_step": int(out.numel() * out.element_size()), "steps": Ke}
 
-    cpu = None
+    cpu = cpu_threaded = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         res = oracle_rate(images.cpu().numpy(), spec)
         gpu_match = all(np.array_equal(s.cpu().numpy(), res["result"]["shifts"]) for s in shifts)
         cpu = {k: v for k, v in res.items() if k != "result"}
         cpu["value"] = round(cpu["value"], 3)
         cpu["gpu_shifts_equal_oracle"] = bool(gpu_match)
+        if args.cpu_threads != 1:
+            nthr = args.cpu_threads if args.cpu_threads > 0 else len(os.sched_getaffinity(0))
+            cpu_threaded = oracle_rate_threaded(images.cpu().numpy(), spec, nthr)
 
     if rank == 0:
         line = {
@@ -456,6 +497,7 @@ def run_gb300(args):
             "stages": stages,
             "roofline": roofline,
             "cpu_baseline": cpu,
+            "cpu_baseline_threaded": cpu_threaded,
             "e2e": e2e,
             "gpu_launches": K * kernels_per_step(spec),
             "clocks": clocks,
