@@ -136,10 +136,23 @@ CopyPipe *copy_pipe() {
     CopyPipe &p = g_pipes[dev];
     std::lock_guard<std::mutex> g(g_pipes_mu);
     if (!p.ready) {
-        if (cudaStreamCreateWithFlags(&p.copy, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
-        if (cudaEventCreateWithFlags(&p.start, cudaEventDisableTiming) != cudaSuccess) return nullptr;
-        for (int k = 0; k < kMaxBands; ++k)
-            if (cudaEventCreateWithFlags(&p.band[k], cudaEventDisableTiming) != cudaSuccess) return nullptr;
+        // all or nothing: a failed setup releases what it made, and the next
+        // call tries again from scratch
+        cudaStream_t copy = nullptr;
+        cudaEvent_t ev[1 + kMaxBands] = {};
+        bool ok = cudaStreamCreateWithFlags(&copy, cudaStreamNonBlocking) == cudaSuccess;
+        for (int k = 0; ok && k <= kMaxBands; ++k)
+            ok = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) {
+            for (cudaEvent_t e : ev)
+                if (e) cudaEventDestroy(e);
+            if (copy) cudaStreamDestroy(copy);
+            cudaGetLastError();
+            return nullptr;
+        }
+        p.copy = copy;
+        p.start = ev[0];
+        for (int k = 0; k < kMaxBands; ++k) p.band[k] = ev[1 + k];
         p.ready = true;
     }
     return &p;
