@@ -262,7 +262,9 @@ int mtb_batch_run(mtb_batch_t *batch, void *stream);
  * The window budget trades the brute-force windows of the coarse levels
  * (Sec. III-B's search, counted for every candidate of the reachable window at
  * once) against one 9-candidate hop per level; results are the same either
- * way.  Synchronous. */
+ * way.  Synchronous.  No run of the batch may still be in flight on another
+ * stream: the tables a run reads are rewritten.  If a timing fails, the best
+ * setting found so far is rebuilt and the error returned. */
 int mtb_batch_tune(mtb_batch_t *batch, int reps, void *stream);
 
 /* The batch's settings:
@@ -278,14 +280,16 @@ int mtb_batch_config(const mtb_batch_t *batch, int *values, int n_values);
 /* Sets the batch's settings in the layout of mtb_batch_config.  values[3] is
  * ignored.  Each other value must be one of the autotuner's candidates
  * (MTB_ERR_INVALID_ARG otherwise).  n_values >= 5.  Replans the batch and
- * recaptures its graph; on an error the previous settings stay. */
+ * recaptures its graph; on an error the previous settings stay.  As for
+ * mtb_batch_tune, no run of the batch may be in flight. */
 int mtb_batch_set_config(mtb_batch_t *batch, const int *values, int n_values);
 
 /* Waits for `stream`, then returns MTB_OK or the first stack's non-zero status
  * word (MTB_ERR_TIMEOUT if a bounded device wait gave up). */
 int mtb_batch_status(mtb_batch_t *batch, void *stream);
 
-/* Frees the batch (and its workspace if it allocated it).  NULL is ignored. */
+/* Frees the batch (and its workspace if it allocated it) once its runs are
+ * complete.  NULL is ignored. */
 void mtb_batch_destroy(mtb_batch_t *batch);
 
 /* Size of the fixed device scratch array used by mtb_align_stack_noalloc:
@@ -389,7 +393,9 @@ size_t mtb_job_bytes(const mtb_job_t *job);
 
 /* Checks the configuration (MTB_ERR_INVALID_ARG before any CUDA call), then
  * allocates the arena on the current device (MTB_ERR_OOM if it cannot), the
- * streams and a pinned result area per slot, and starts the worker. */
+ * streams and a pinned result area per slot, and starts the worker.  After
+ * this call the server allocates nothing on the host per job beyond the job's
+ * record in mtb_server_submit (MTB_ERR_OOM if that fails). */
 int mtb_server_create(const mtb_server_config_t *config, mtb_server_t **out);
 
 /* Queues a job; *job_id receives its id.  MTB_ERR_INVALID_ARG for an invalid

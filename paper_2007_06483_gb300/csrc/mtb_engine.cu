@@ -436,11 +436,9 @@ int stack_layout(const mtb_stack_desc_t &sd, mtb_layout_t *L) {
 size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
 // Plans all stacks with b->tuning, uploads the tables and captures the graph.
-int batch_build(mtb_batch *b) {
-    if (b->graph) {
-        cudaGraphExecDestroy(b->graph);
-        b->graph = nullptr;
-    }
+// A plan that fails (MTB_ERR_INVALID_ARG) leaves the batch as it was; a failed
+// upload leaves it refusing to run (MTB_ERR_CUDA from batch_launch).
+int batch_build_tables(mtb_batch *b) {
     const int n = b->count;
     long long total_tiles = 0;
     for (int s = 0; s < n; ++s) total_tiles += stack_tiles(b->layouts[s]);
@@ -455,7 +453,7 @@ int batch_build(mtb_batch *b) {
     // phase-major queue: phase_first over all stacks, stack_first within each phase
     std::vector<int> stack_first((size_t)kPhases * (n + 1));
     long long first = 0;
-    EngineArgs &A = b->args;
+    EngineArgs A = b->args;
     for (int ph = 0; ph < kPhases; ++ph) {
         A.phase_first[ph] = (int)first;
         long long within = 0;
@@ -472,13 +470,21 @@ int batch_build(mtb_batch *b) {
     A.n_stacks = n;
     const size_t desc_bytes = align256(sizeof(StackDesc) * n);
     const size_t first_bytes = align256(sizeof(int) * stack_first.size());
+    // the plan holds; from here on the batch's old graph and tables go
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
     if (cudaMemcpy(b->tables, descs.data(), sizeof(StackDesc) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(b->tables + desc_bytes, stack_first.data(), sizeof(int) * stack_first.size(),
-                   cudaMemcpyHostToDevice) != cudaSuccess)
+                   cudaMemcpyHostToDevice) != cudaSuccess) {
+        b->args.total_items = 0;
         return MTB_ERR_CUDA;
+    }
     A.stacks = reinterpret_cast<const StackDesc *>(b->tables);
     A.stack_first = reinterpret_cast<const int *>(b->tables + desc_bytes);
     A.queue = reinterpret_cast<int32_t *>(b->tables + desc_bytes + first_bytes);
+    b->args = A;
     // capture clear + engine in a graph (run without one if capture is refused)
     cudaStream_t cs;
     if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return MTB_ERR_CUDA;
@@ -497,9 +503,21 @@ int batch_build(mtb_batch *b) {
     return MTB_OK;
 }
 
+// batch_build_tables with a failed host allocation reported as MTB_ERR_OOM (no
+// C++ exception leaves the library).  The host vectors are all allocated before
+// the graph capture begins, so no capture is left open.
+int batch_build(mtb_batch *b) {
+    try {
+        return batch_build_tables(b);
+    } catch (...) {
+        return MTB_ERR_OOM;
+    }
+}
+
 int batch_launch(mtb_batch *b, cudaStream_t s) {
     if (b->graph) return cudaGraphLaunch(b->graph, s) == cudaSuccess ? MTB_OK : MTB_ERR_CUDA;
     const EngineArgs &A = b->args;
+    if (A.total_items <= 0) return MTB_ERR_CUDA;  // the last table upload failed
     const int grid = (int)(A.total_items < b->cap ? A.total_items : b->cap);
     if (launch_k(k_engine_clear<true>, dim3(b->count), dim3(1024), s, false, A) != cudaSuccess) return MTB_ERR_CUDA;
     if (launch_k(k_engine<true>, dim3(grid), dim3(kEngineThreads), s, true, A) != cudaSuccess) return MTB_ERR_CUDA;
@@ -528,9 +546,14 @@ int mtb_batch_create(const mtb_stack_desc_t *stacks, int count, void *workspace,
     mtb_batch *b = new (std::nothrow) mtb_batch();
     if (!b) return MTB_ERR_OOM;
     b->count = count;
-    b->user.assign(stacks, stacks + count);
-    b->layouts.resize(count);
-    b->ws_offset.resize(count);
+    try {
+        b->user.assign(stacks, stacks + count);
+        b->layouts.resize(count);
+        b->ws_offset.resize(count);
+    } catch (...) {
+        delete b;
+        return MTB_ERR_OOM;
+    }
     size_t total = 0;
     int rc = MTB_OK;
     for (int s = 0; s < count && rc == MTB_OK; ++s) {
@@ -578,8 +601,12 @@ int mtb_batch_run(mtb_batch_t *b, void *stream) {
 int mtb_batch_tune(mtb_batch_t *b, int reps, void *stream) {
     if (!b || reps < 1 || reps > 100) return MTB_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    cudaEvent_t e0, e1;
-    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return MTB_ERR_CUDA;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        cudaGetLastError();
+        return MTB_ERR_CUDA;
+    }
     auto time_config = [&](float *ms) -> int {
         int rc = batch_build(b);
         if (rc != MTB_OK) return rc;
@@ -615,8 +642,11 @@ int mtb_batch_tune(mtb_batch_t *b, int reps, void *stream) {
             }
         }
     }
+    // the best setting found (the starting one if the first timing failed) is
+    // rebuilt even after a failure, so the batch stays runnable as before
     b->tuning = best;
-    if (rc == MTB_OK) rc = batch_build(b);
+    const int rc_build = batch_build(b);
+    if (rc == MTB_OK) rc = rc_build;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return rc;

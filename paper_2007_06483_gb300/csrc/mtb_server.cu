@@ -22,7 +22,6 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
-#include <map>
 #include <memory>
 #include <mutex>
 #include <new>
@@ -30,56 +29,17 @@
 #include <unordered_map>
 #include <vector>
 
+#include "mtb_arena.h"
 #include "mtb_internal.cuh"
 
 namespace {
 
 using Clock = std::chrono::steady_clock;
 
-constexpr size_t kArenaAlign = 256;
+using mtb::kArenaAlign;
+using mtb::round_up;
 
-size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
-
-// First-fit allocator over [0, size), in kArenaAlign units; free blocks merge.
-class Arena {
-  public:
-    explicit Arena(size_t size) { free_[0] = size; }
-    bool alloc(size_t bytes, size_t *off) {
-        bytes = round_up(bytes, kArenaAlign);
-        for (auto it = free_.begin(); it != free_.end(); ++it) {
-            if (it->second < bytes) continue;
-            *off = it->first;
-            const size_t rest = it->second - bytes, start = it->first + bytes;
-            free_.erase(it);
-            if (rest) free_[start] = rest;
-            in_use_ += bytes;
-            return true;
-        }
-        return false;
-    }
-    void release(size_t off, size_t bytes) {
-        bytes = round_up(bytes, kArenaAlign);
-        in_use_ -= bytes;
-        auto it = free_.emplace(off, bytes).first;
-        auto next = std::next(it);
-        if (next != free_.end() && it->first + it->second == next->first) {
-            it->second += next->second;
-            free_.erase(next);
-        }
-        if (it != free_.begin()) {
-            auto prev = std::prev(it);
-            if (prev->first + prev->second == it->first) {
-                prev->second += it->second;
-                free_.erase(it);
-            }
-        }
-    }
-    size_t in_use() const { return in_use_; }
-
-  private:
-    std::map<size_t, size_t> free_;
-    size_t in_use_ = 0;
-};
+using Arena = mtb::Arena<MTB_SERVER_MAX_SLOTS>;  // at most `slots` jobs hold memory
 
 constexpr int kRunning = 1;  // job status while queued or on the GPU
 
@@ -276,8 +236,17 @@ int mtb_server_create(const mtb_server_config_t *config, mtb_server_t **out) {
     s->cfg = *config;
     s->cfg.budget_bytes = config->budget_bytes / kArenaAlign * kArenaAlign;
     const int S = s->cfg.slots, C = s->cfg.copy_streams;
-    s->running.resize(S);
-    s->ctx.resize(S);
+    try {  // host allocations first: after this point nothing throws
+        s->running.resize(S);
+        s->ctx.resize(S);
+        s->compute.reserve(S);
+        s->copy.reserve(C);
+        s->copied.reserve((size_t)S * C);
+        s->arena.reset(new Arena(s->cfg.budget_bytes));
+    } catch (...) {
+        delete s;
+        return MTB_ERR_OOM;
+    }
     if (cudaGetDevice(&s->device) != cudaSuccess) rc = MTB_ERR_CUDA;
     void *p = nullptr;
     if (rc == MTB_OK && cudaMalloc(&p, s->cfg.budget_bytes) != cudaSuccess) rc = MTB_ERR_OOM;
@@ -308,15 +277,25 @@ int mtb_server_create(const mtb_server_config_t *config, mtb_server_t **out) {
         delete s;
         return rc;
     }
-    s->arena.reset(new Arena(s->cfg.budget_bytes));
-    s->worker = std::thread(worker_loop, s);
+    try {
+        s->worker = std::thread(worker_loop, s);
+    } catch (...) {
+        release_resources(s);
+        delete s;
+        return MTB_ERR_OOM;
+    }
     *out = s;
     return MTB_OK;
 }
 
 int mtb_server_submit(mtb_server_t *s, const mtb_job_t *job, uint64_t *job_id) {
     if (!s || !job || !job_id || !job->host_images || !job->host_shifts_out) return MTB_ERR_INVALID_ARG;
-    auto j = std::make_shared<Job>();
+    std::shared_ptr<Job> j;
+    try {
+        j = std::make_shared<Job>();
+    } catch (...) {
+        return MTB_ERR_OOM;
+    }
     j->desc = *job;
     j->bytes = job_bytes(*job, &j->layout);
     if (j->bytes == 0) return MTB_ERR_INVALID_ARG;
@@ -326,10 +305,16 @@ int mtb_server_submit(mtb_server_t *s, const mtb_job_t *job, uint64_t *job_id) {
         ++s->refused;
         return MTB_ERR_BUSY;
     }
-    j->id = s->next_id++;
+    j->id = s->next_id;
     j->t_submit = Clock::now();
-    s->jobs[j->id] = j;
-    s->pending.push_back(j);
+    try {
+        s->jobs.emplace(j->id, j);
+        s->pending.push_back(j);
+    } catch (...) {
+        s->jobs.erase(j->id);
+        return MTB_ERR_OOM;
+    }
+    ++s->next_id;
     s->cv_work.notify_one();
     *job_id = j->id;
     return MTB_OK;
