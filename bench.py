@@ -69,10 +69,10 @@ FALLBACK_HBM_GBS = 6800.0
 # sources at capture time; reported only while those sources are unchanged.
 NCU_TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum (cold cache), one
-    # launch each: k_pyramid of the 4000x3000x3 stack (109.70 MB read + 7.02 MB
-    # written) and k_apply_shifts of the 6000x4000x7 stack (496.90 + 458.23 MB)
-    ("k_pyramid", "stack4000x3000x3"): {"bytes": 116722432, "sources_sha256": "cc9d865048422a90249c4f58f1fa03e3581da46f126e89acf788ede5240e2f36"},
-    ("k_apply_shifts", "apply6000x4000x7"): {"bytes": 955125760, "sources_sha256": "4b7f3ffd94b326a5d686199ec8fa8202e960c3c889570379abf50ac3b10a00c0"},
+    # launch each: k_pyramid of the 4000x3000x3 stack (109.70 MB read + 6.95 MB
+    # written) and k_apply_shifts of the 6000x4000x7 stack (496.81 + 458.26 MB)
+    ("k_pyramid", "stack4000x3000x3"): {"bytes": 116647680, "sources_sha256": "51d50f00dfb4fe6bf0b3fbd829edfbd37d05433985f0057cd6a55eace28f9b84"},
+    ("k_apply_shifts", "apply6000x4000x7"): {"bytes": 955071744, "sources_sha256": "e265c02bbfa6e0cda0bd4c35ae4a6118438da478c9b3a3a35471b1d9ce84ba18"},
 }
 
 
