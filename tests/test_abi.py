@@ -117,3 +117,17 @@ def test_invalid_sizes_give_zero_workspace(mtb_lib):
     assert mtb_lib.workspace_bytes(1, 64, 64, 3) == 0
     assert mtb_lib.workspace_bytes(2, 64, 64, 8) == 0
     assert mtb_lib.host_workspace_bytes(2, 0, 64, 1) == 0
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    """No CPU fallback: without the built library every call raises."""
+    import paper_2007_06483_gb300 as mtb
+
+    monkeypatch.setattr(mtb, "LIB_PATH", os.path.join(ROOT, "_no_such_dir", "libmtb_gb300.so"))
+    monkeypatch.setattr(mtb, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        mtb.lib()
+    with pytest.raises(RuntimeError, match="not built"):
+        mtb.workspace_bytes(3, 64, 48, 3)
+    with pytest.raises(RuntimeError, match="not built"):
+        mtb.status_string(0)
