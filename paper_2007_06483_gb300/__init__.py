@@ -525,6 +525,9 @@ class Server:
         n, w, h = _dims(images)
         if out is None:
             out = torch.empty((n, 2), dtype=torch.int32)
+        elif out.device.type != "cpu" or out.dtype != torch.int32 or tuple(out.shape) != (n, 2) or \
+                not out.is_contiguous():
+            raise ValueError("out must be a contiguous host int32 [n, 2] tensor")
         job = Job(images.data_ptr(), n, w, h, int(levels), int(noise_tol), int(ref_idx), out.data_ptr())
         jid = ctypes.c_uint64()
         _check(lib().mtb_server_submit(self._h, ctypes.byref(job), ctypes.byref(jid)), "mtb_server_submit")

@@ -149,3 +149,20 @@ def test_back_pressure_and_refusals(mtb_lib):
         assert srv.poll(a) == mtb_lib.MTB_ERR_INVALID_ARG  # forgotten after wait
     alone = _alone(mtb_lib, [jobs[0]])[0]
     assert torch.equal(sa, alone) and torch.equal(sb, alone)
+
+
+@pytest.mark.parametrize("bad", ["short", "int64", "strided"])
+def test_submit_rejects_bad_out_on_host(bad):
+    """The completion callback writes n x 2 int32 into `out`: anything else is
+    refused before the job reaches the library (no server or GPU needed)."""
+    import paper_2007_06483_gb300 as mtb
+
+    srv = mtb.Server.__new__(mtb.Server)  # checks run before any library call
+    srv._h = None
+    srv._jobs = {}
+    images = torch.zeros((3, 8, 16, 3), dtype=torch.uint8)
+    out = {"short": torch.empty((2, 2), dtype=torch.int32),
+           "int64": torch.empty((3, 2), dtype=torch.int64),
+           "strided": torch.empty((3, 4), dtype=torch.int32)[:, ::2]}[bad]
+    with pytest.raises(ValueError, match="out must be"):
+        srv.submit(images, 3, out=out)
