@@ -197,6 +197,38 @@ def _dims(images):
     return int(n), int(w), int(h)
 
 
+def _cuda_dims(images):
+    """_dims for the entry points that read the images from device memory."""
+    n, w, h = _dims(images)
+    if images.device.type != "cuda":
+        raise ValueError("images must be a CUDA tensor")
+    return n, w, h
+
+
+def _out(t, shape, dev, what):
+    """t (or None) as an output the library writes: a contiguous 32-bit integer
+    tensor of `shape` on device `dev`."""
+    import torch
+
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or t.device != dev or t.element_size() != 4 or t.dtype.is_floating_point or \
+            tuple(t.shape) != tuple(shape) or not t.is_contiguous():
+        raise ValueError(f"{what} must be a contiguous 32-bit integer tensor {list(shape)} on {dev}")
+    return t
+
+
+def _workspace(ws, dev):
+    """(pointer, bytes) of a caller workspace on device `dev`, (None, 0) for none."""
+    import torch
+
+    if ws is None:
+        return None, 0
+    if not isinstance(ws, torch.Tensor) or ws.device != dev or not ws.is_contiguous():
+        raise ValueError(f"workspace must be a contiguous tensor on {dev}")
+    return ws.data_ptr(), ws.numel() * ws.element_size()
+
+
 def new_workspace(n: int, w: int, h: int, levels: int, device="cuda"):
     import torch
 
@@ -213,16 +245,14 @@ def align_stack(images, levels: int, noise_tol: int = 4, ref_idx: int = 0, *, le
     [n, levels, 2] per-level shifts).  `out` may hold the int32 [n, 2] result."""
     import torch
 
-    n, w, h = _dims(images)
+    n, w, h = _cuda_dims(images)
     dev = images.device
-    shifts = out if out is not None else torch.empty((n, 2), dtype=torch.int32, device=dev)
+    shifts = _out(out, (n, 2), dev, "out") if out is not None else torch.empty((n, 2), dtype=torch.int32, device=dev)
     errs = lsh = None
     if level_outputs:
         errs = torch.empty((n, levels, 9), dtype=torch.int32, device=dev)  # viewed as uint32
         lsh = torch.empty((n, levels, 2), dtype=torch.int32, device=dev)
-    ws_ptr, ws_bytes = None, 0
-    if workspace is not None:
-        ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
+    ws_ptr, ws_bytes = _workspace(workspace, dev)
     if errs is None and workspace is None:
         rc = lib().mtb_align_stack(images.data_ptr(), n, w, h, levels, noise_tol, ref_idx, shifts.data_ptr(),
                                    _stream(stream))
@@ -242,16 +272,14 @@ def align_stack_chain(images, levels: int, noise_tol: int = 4, ref_idx: int = 0,
     align_stack (per-level rows hold the neighbour pair's values)."""
     import torch
 
-    n, w, h = _dims(images)
+    n, w, h = _cuda_dims(images)
     dev = images.device
-    shifts = out if out is not None else torch.empty((n, 2), dtype=torch.int32, device=dev)
+    shifts = _out(out, (n, 2), dev, "out") if out is not None else torch.empty((n, 2), dtype=torch.int32, device=dev)
     errs = lsh = None
     if level_outputs:
         errs = torch.empty((n, levels, 9), dtype=torch.int32, device=dev)  # viewed as uint32
         lsh = torch.empty((n, levels, 2), dtype=torch.int32, device=dev)
-    ws_ptr, ws_bytes = None, 0
-    if workspace is not None:
-        ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
+    ws_ptr, ws_bytes = _workspace(workspace, dev)
     _check(lib().mtb_align_stack_chain(images.data_ptr(), n, w, h, levels, noise_tol, ref_idx, shifts.data_ptr(),
                                        _ptr(errs), _ptr(lsh), ws_ptr, ws_bytes, _stream(stream)),
            "mtb_align_stack_chain")
@@ -267,40 +295,50 @@ def align_quadrants(images, levels: int, noise_tol: int = 4, ref_idx: int = 0, r
     the device."""
     import torch
 
-    n, w, h = _dims(images)
+    n, w, h = _cuda_dims(images)
     dev = images.device
     qs = torch.empty((n, 4, 2), dtype=torch.int32, device=dev)
     flags = torch.empty((n,), dtype=torch.int32, device=dev)
-    ws_ptr, ws_bytes = None, 0
-    if workspace is not None:
-        ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
+    ws_ptr, ws_bytes = _workspace(workspace, dev)
     _check(lib().mtb_align_quadrants(images.data_ptr(), n, w, h, levels, noise_tol, ref_idx, rot_tol, qs.data_ptr(),
                                      flags.data_ptr(), ws_ptr, ws_bytes, _stream(stream)), "mtb_align_quadrants")
     return qs, flags
 
 
 def build_pyramids(images, levels: int, workspace, stream=None):
-    n, w, h = _dims(images)
-    _check(lib().mtb_build_pyramids(images.data_ptr(), n, w, h, levels, workspace.data_ptr(), workspace.numel(),
-                                    _stream(stream)), "mtb_build_pyramids")
+    n, w, h = _cuda_dims(images)
+    ws_ptr, ws_bytes = _workspace(workspace, images.device)
+    _check(lib().mtb_build_pyramids(images.data_ptr(), n, w, h, levels, ws_ptr, ws_bytes, _stream(stream)),
+           "mtb_build_pyramids")
+
+
+def _stage_workspace(workspace):
+    if workspace is None or workspace.device.type != "cuda":
+        raise ValueError("workspace must be a CUDA tensor")
+    return _workspace(workspace, workspace.device)
 
 
 def build_bitmaps(n: int, w: int, h: int, levels: int, noise_tol: int, workspace, stream=None):
-    _check(lib().mtb_build_bitmaps(n, w, h, levels, noise_tol, workspace.data_ptr(), workspace.numel(),
-                                   _stream(stream)), "mtb_build_bitmaps")
+    ws_ptr, ws_bytes = _stage_workspace(workspace)
+    _check(lib().mtb_build_bitmaps(n, w, h, levels, noise_tol, ws_ptr, ws_bytes, _stream(stream)),
+           "mtb_build_bitmaps")
 
 
 def search_shifts(n: int, w: int, h: int, levels: int, ref_idx: int, workspace, shifts_out=None,
                   level_errs_out=None, level_shifts_out=None, stream=None):
-    _check(lib().mtb_search_shifts(n, w, h, levels, ref_idx, workspace.data_ptr(), workspace.numel(),
-                                   _ptr(shifts_out), _ptr(level_errs_out), _ptr(level_shifts_out), _stream(stream)),
-           "mtb_search_shifts")
+    ws_ptr, ws_bytes = _stage_workspace(workspace)
+    dev = workspace.device
+    sh = _out(shifts_out, (n, 2), dev, "shifts_out")
+    er = _out(level_errs_out, (n, levels, 9), dev, "level_errs_out")
+    ls = _out(level_shifts_out, (n, levels, 2), dev, "level_shifts_out")
+    _check(lib().mtb_search_shifts(n, w, h, levels, ref_idx, ws_ptr, ws_bytes, _ptr(sh), _ptr(er), _ptr(ls),
+                                   _stream(stream)), "mtb_search_shifts")
 
 
 def workspace_status(workspace, n: int, w: int, h: int, levels: int, stream=None) -> int:
     """Status word of the last search in `workspace` (MTB_OK or MTB_ERR_TIMEOUT)."""
-    return int(lib().mtb_workspace_status(workspace.data_ptr(), workspace.numel(), n, w, h, levels,
-                                          _stream(stream)))
+    ws_ptr, ws_bytes = _stage_workspace(workspace)
+    return int(lib().mtb_workspace_status(ws_ptr, ws_bytes, n, w, h, levels, _stream(stream)))
 
 
 def get_last_status(stream=None) -> int:
@@ -318,6 +356,8 @@ def align_stack_host(images, levels: int, noise_tol: int = 4, ref_idx: int = 0, 
     import torch
 
     n, w, h = _dims(images)
+    if images.device.type != "cpu":
+        raise ValueError("images must be a CPU tensor (the call copies them to the device)")
     if out is None:
         out = torch.empty((n, 2), dtype=torch.int32, pin_memory=images.is_pinned())
     elif out.device.type != "cpu" or out.dtype != torch.int32 or tuple(out.shape) != (n, 2) or \
@@ -325,7 +365,9 @@ def align_stack_host(images, levels: int, noise_tol: int = 4, ref_idx: int = 0, 
         raise ValueError("out must be a contiguous host int32 [n, 2] tensor")
     ws_ptr, ws_bytes = None, 0
     if device_workspace is not None:
-        ws_ptr, ws_bytes = device_workspace.data_ptr(), device_workspace.numel()
+        if device_workspace.device.type != "cuda":
+            raise ValueError("device_workspace must be a CUDA tensor")
+        ws_ptr, ws_bytes = _workspace(device_workspace, device_workspace.device)
     _check(lib().mtb_align_stack_host(images.data_ptr(), n, w, h, levels, noise_tol, ref_idx, out.data_ptr(),
                                       ws_ptr, ws_bytes, _stream(stream)), "mtb_align_stack_host")
     return out
@@ -373,11 +415,17 @@ def apply_shifts(images, shifts, fill: int = MTB_FILL_ZERO, *, out=None, stream=
     MTB_FILL_EDGE.  Returns out ([n, h, w, 3], allocated here if not given)."""
     import torch
 
-    n, w, h = _dims(images)
+    n, w, h = _cuda_dims(images)
     if shifts.dtype != torch.int32 or shifts.device != images.device or tuple(shifts.shape) != (n, 2):
         raise ValueError("shifts must be an int32 tensor [n, 2] on the images' device")
     if out is None:
         out = torch.empty_like(images)
+    elif out.device != images.device or out.dtype != torch.uint8 or out.shape != images.shape or \
+            not out.is_contiguous():
+        raise ValueError("out must be a contiguous uint8 tensor shaped like images, on their device")
+    nbytes = images.numel()
+    if out.data_ptr() < images.data_ptr() + nbytes and images.data_ptr() < out.data_ptr() + nbytes:
+        raise ValueError("out must not overlap images")
     _check(lib().mtb_apply_shifts(images.data_ptr(), n, w, h, shifts.contiguous().data_ptr(), int(fill),
                                   out.data_ptr(), _stream(stream)), "mtb_apply_shifts")
     return out
@@ -402,7 +450,7 @@ def align_stack_noalloc(images, levels: int, noise_tol: int = 4, ref_idx: int = 
         fn.restype = I
         fn.argtypes = [P, I, I, I, I, I, I, P, P, P, P]
         _noalloc_fn = fn
-    n, w, h = _dims(images)
+    n, w, h = _cuda_dims(images)
     dev = images.device
     shifts = torch.empty((n, 2), dtype=torch.int32, device=dev)
     errs = torch.empty((n, levels, 9), dtype=torch.int32, device=dev)
@@ -428,7 +476,7 @@ class Batch:
         self.shifts, self.level_errs, self.level_shifts = [], [], []
         for k, st in enumerate(stacks):
             imgs = st["images"]
-            n, w, h = _dims(imgs)
+            n, w, h = _cuda_dims(imgs)
             L = int(st["levels"])
             dev = imgs.device
             sh = torch.zeros((n, 2), dtype=torch.int32, device=dev)
@@ -444,7 +492,9 @@ class Batch:
         handle = ctypes.c_void_p()
         ws_ptr, ws_bytes = None, 0
         if workspace is not None:
-            ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel()
+            if not stacks:
+                raise ValueError("a batch needs at least one stack")
+            ws_ptr, ws_bytes = _workspace(workspace, stacks[0]["images"].device)
             self._keep.append(workspace)
         _check(lib().mtb_batch_create(ctypes.cast(descs, ctypes.c_void_p), len(stacks), ws_ptr, ws_bytes,
                                       ctypes.byref(handle)), "mtb_batch_create")

@@ -131,3 +131,52 @@ def test_missing_library_fails_loudly(monkeypatch):
         mtb.workspace_bytes(3, 64, 48, 3)
     with pytest.raises(RuntimeError, match="not built"):
         mtb.status_string(0)
+
+
+def test_binding_rejects_misplaced_tensors_on_host():
+    """The binding refuses, before any library call, tensors on the wrong side of
+    the host/device boundary, and outputs the library could overrun."""
+    import torch
+
+    import paper_2007_06483_gb300 as mtb
+
+    cpu_imgs = torch.zeros((2, 8, 16, 3), dtype=torch.uint8)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        mtb.align_stack(cpu_imgs, 2)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        mtb.align_stack_chain(cpu_imgs, 2)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        mtb.align_quadrants(cpu_imgs, 2)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        mtb.apply_shifts(cpu_imgs, torch.zeros((2, 2), dtype=torch.int32))
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        mtb.build_bitmaps(2, 16, 8, 2, 4, torch.zeros(1024, dtype=torch.uint8))
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        mtb.search_shifts(2, 16, 8, 2, 0, torch.zeros(1024, dtype=torch.uint8))
+    meta_imgs = torch.empty((2, 8, 16, 3), dtype=torch.uint8, device="meta")
+    with pytest.raises(ValueError, match="CPU tensor"):
+        mtb.align_stack_host(meta_imgs, 2)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        mtb.align_stack_host(cpu_imgs, 2, device_workspace=torch.zeros(1024, dtype=torch.uint8))
+
+
+@pytest.mark.parametrize("bad", ["shape", "dtype", "float", "strided", "device"])
+def test_output_checks(bad):
+    import torch
+
+    import paper_2007_06483_gb300 as mtb
+
+    dev = torch.device("cpu")
+    good = torch.empty((3, 2), dtype=torch.int32)
+    assert mtb._out(good, (3, 2), dev, "out") is good
+    assert mtb._out(None, (3, 2), dev, "out") is None
+    t = {"shape": torch.empty((2, 2), dtype=torch.int32),
+         "dtype": torch.empty((3, 2), dtype=torch.int64),
+         "float": torch.empty((3, 2), dtype=torch.float32),
+         "strided": torch.empty((3, 4), dtype=torch.int32)[:, ::2],
+         "device": torch.empty((3, 2), dtype=torch.int32, device="meta")}[bad]
+    with pytest.raises(ValueError, match="out must be"):
+        mtb._out(t, (3, 2), dev, "out")
+    with pytest.raises(ValueError, match="workspace"):
+        mtb._workspace(torch.empty(64, dtype=torch.uint8, device="meta"), dev)
+    assert mtb._workspace(torch.empty(64, dtype=torch.int32), dev)[1] == 256

@@ -72,3 +72,13 @@ def test_apply_full_size_stack(mtb_lib, oracle_mod):
         torch.cuda.synchronize()
         want = oracle_mod.apply_shifts(imgs.cpu().numpy(), sh, fill)
         assert np.array_equal(out.cpu().numpy(), want), fill
+
+
+@pytest.mark.gpu
+def test_apply_binding_rejects_bad_out(mtb_lib):
+    d = torch.zeros((2, 8, 16, 3), dtype=torch.uint8, device="cuda")
+    sh = torch.zeros((2, 2), dtype=torch.int32, device="cuda")
+    with pytest.raises(ValueError, match="overlap"):
+        mtb_lib.apply_shifts(d, sh, 0, out=d)
+    with pytest.raises(ValueError, match="shaped like"):
+        mtb_lib.apply_shifts(d, sh, 0, out=torch.zeros((2, 8, 15, 3), dtype=torch.uint8, device="cuda"))

@@ -187,3 +187,18 @@ def test_last_status_per_stream(mtb_lib):
     assert mtb_lib.get_last_status(s2) == mtb_lib.MTB_OK
     assert mtb_lib.get_last_status(s1) == mtb_lib.MTB_ERR_TIMEOUT
     assert np.array_equal(out.cpu().numpy(), synth.expected_shifts(spec))
+
+
+@pytest.mark.gpu
+def test_binding_rejects_outputs_it_could_overrun(mtb_lib):
+    imgs = torch.zeros((3, 32, 64, 3), dtype=torch.uint8, device="cuda")
+    with pytest.raises(ValueError, match="out must be"):
+        mtb_lib.align_stack(imgs, 3, out=torch.empty((2, 2), dtype=torch.int32, device="cuda"))
+    with pytest.raises(ValueError, match="out must be"):
+        mtb_lib.align_stack_chain(imgs, 3, out=torch.empty((3, 2), dtype=torch.int64, device="cuda"))
+    ws = mtb_lib.new_workspace(3, 64, 32, 3)
+    with pytest.raises(ValueError, match="level_errs_out must be"):
+        mtb_lib.search_shifts(3, 64, 32, 3, 0, ws, level_errs_out=torch.empty((3, 2, 9), dtype=torch.int32,
+                                                                               device="cuda"))
+    with pytest.raises(ValueError, match="workspace must be"):
+        mtb_lib.align_stack(imgs, 3, workspace=ws[::2])
