@@ -6,16 +6,26 @@ mtb_align_stack_ex call, which enqueues the pyramid pass (k_clear, k_pyramid),
 the bitmap pass (k_bitmaps) and the coarse-to-fine shift search (k_search,
 which starts while the bitmaps are still being packed), chained by
 programmatic dependent launch.  The
-default workload is the 4000x3000 stack of 3 exposures (2 pairs, 7 levels).
-The metric is aligned MPix/s: full-resolution pixels of every aligned pair
-divided by the step time.  The K timed steps run back to back between two
-events: an event between two steps would serialise one step's search with the
-next step's launches. p50/p99 latency comes from a second loop with events
-around each step (at least 100 timed steps after 10 more warm-ups). A third
-loop of K steps times the same work through the three stage calls
-(mtb_build_pyramids, mtb_build_bitmaps, mtb_search_shifts) with CUDA events
-between them on the launching stream: the split by stage, and the duration of
-the dominant kernel (k_pyramid) for the roofline.
+default workload is the 6000x4000 stack of 7 exposures (6 pairs, 8 levels), the
+largest plain stack.  The metric is aligned MPix/s: full-resolution pixels of
+every aligned pair divided by the step time.  The K timed steps run back to
+back between two events: an event between two steps would serialise one step's
+search with the next step's launches.  That K-step region is timed again and
+again (each time bracketed by a barrier and a synchronize) until the regions
+add up to at least --min-timed-s of wall time, so that the clock sampler sees
+the GPU under load; the value is the mean over all of them. p50/p99 latency
+comes from a second loop with events around each step (at least 100 timed
+steps after 10 more warm-ups). A third loop times the same work through the
+three stage calls (mtb_build_pyramids, mtb_build_bitmaps, mtb_search_shifts)
+with CUDA events between them on the launching stream: the split by stage.  The
+roofline names the stage with the largest share of that split, and every
+stage's fraction of the peak is listed.
+
+The default line also carries a compact batched-vs-plain record (`batch`): the
+uneven stacks of the batched form (--batch-count of them, 256 by default) in
+one persistent launch against the plain path on the same stacks, with every
+stack's shifts and per-level errors compared with the oracle (run on every
+usable host core, outside the timed regions).
 
 Inputs and workspaces rotate over several device copies, so between two uses of
 one buffer more than 3x the L2 capacity is written and read: every step starts
@@ -82,7 +92,13 @@ def parse_args(argv=None):
     p.add_argument("--steps", type=int, default=50)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=("gb300", "reference"), default="gb300")
-    p.add_argument("--workload", default="stack4000x3000x3")
+    p.add_argument("--workload", default="stack6000x4000x7")
+    p.add_argument("--min-timed-s", type=float, default=0.5,
+                   help="repeat the K-step timed region until the regions add up to this many seconds")
+    p.add_argument("--batch-count", type=int, default=256,
+                   help="stacks of the batched-vs-plain record in the default line (0: leave it out)")
+    p.add_argument("--profile-steps", type=int, default=0,
+                   help="only run this many plain steps of the workload (for ncu captures) and exit")
     p.add_argument("--buffers", type=int, default=4, help="device copies rotated over the steps")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-threads", type=int, default=0,
@@ -160,8 +176,11 @@ def kernels_per_step(spec) -> int:
 
 KERNEL_SOURCES = {  # the files each recorded kernel is built from
     "k_pyramid": ("mtb_pyramid.cu", "mtb_pyramid_dev.cuh", "mtb_device.cuh", "mtb_internal.cuh"),
+    "k_bitmaps": ("mtb_bitmaps.cu", "mtb_bitmaps_dev.cuh", "mtb_device.cuh", "mtb_internal.cuh"),
+    "k_search": ("mtb_search.cu", "mtb_search_dev.cuh", "mtb_device.cuh", "mtb_internal.cuh"),
     "k_apply_shifts": ("mtb_apply.cu", "mtb_internal.cuh"),
 }
+STAGE_KERNEL = {"pyramid": "k_pyramid", "bitmaps": "k_bitmaps", "search": "k_search"}
 
 
 def kernel_sources_digest(kernel: str) -> str:
@@ -326,6 +345,126 @@ def oracle_rate_threaded(images_np, spec, threads: int, budget_s: float = 8.0) -
             "host": host_cpu()}
 
 
+def oracle_many(jobs, threads: int) -> list:
+    """The single-threaded oracle over many stacks at once, one stack per task
+    on `threads` host threads (the C oracle is reentrant and its calls release
+    the GIL).  jobs: callables returning (images uint8 [n, h, w, 3] numpy,
+    levels, noise_tol, ref); a job's host copy is made inside its task, so at
+    most `threads` stacks are held in host memory at a time.  Returns each
+    stack's oracle result in job order."""
+    import concurrent.futures as cf
+
+    import oracle
+
+    oracle.default()  # loaded once, before the threads
+
+    def one(job):
+        imgs, levels, tol, ref = job()
+        return oracle.align_stack(imgs, levels, tol, ref)
+
+    with cf.ThreadPoolExecutor(max_workers=max(1, threads)) as ex:
+        return list(ex.map(one, jobs))
+
+
+def usable_cores() -> int:
+    return len(os.sched_getaffinity(0))
+
+
+def batch_record(count: int, dev, stream, warmup: int, steps: int, oracle_check: bool = True,
+                 sampler=None) -> dict:
+    """Uneven stacks (synth.batch_specs) in one persistent graph-captured launch
+    after the autotuner, against the plain per-stack path on the same stacks;
+    every stack's shifts and per-level errors compared with the plain path and,
+    when oracle_check, with the oracle (on every usable host core, outside the
+    timed regions)."""
+    import numpy as np
+    import torch
+
+    import paper_2007_06483_gb300 as mtb
+    from paper_2007_06483_gb300 import synth
+
+    specs = synth.batch_specs(count)
+    stacks = [{"images": synth.make_stack(sp, dev), "levels": sp.levels, "noise_tol": sp.noise_tol,
+               "ref_idx": sp.ref} for sp in specs]
+    pixels = sum(sp.aligned_pixels for sp in specs)
+    abytes = sum(sum(algorithmic_bytes(sp).values()) for sp in specs)
+    t_tune = time.perf_counter()
+    batch = mtb.Batch(stacks, level_outputs=True)
+    batch.tune(reps=2, stream=stream)
+    t_tune = time.perf_counter() - t_tune
+    cfg = batch.config()
+    for _ in range(max(3, warmup)):
+        batch.run(stream)
+    torch.cuda.synchronize(dev)
+    K = max(1, steps)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(K)]
+    if sampler is not None:
+        sampler.start()
+    for k in range(K):
+        evs[k][0].record(stream)
+        batch.run(stream)
+        evs[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop() if sampler is not None else None
+    status = batch.status()
+    step_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    ms = evs[0][0].elapsed_time(evs[-1][1]) / K
+    expected_ok = sum(np.array_equal(batch.shifts[k].cpu().numpy(), synth.expected_shifts(sp))
+                      for k, sp in enumerate(specs))
+
+    # the same stacks through the plain path, one stack after the other
+    wss = [mtb.new_workspace(sp.n, sp.w, sp.h, sp.levels, device=dev) for sp in specs]
+    outs = [torch.empty((sp.n, 2), dtype=torch.int32, device=dev) for sp in specs]
+
+    def plain():
+        for k, st in enumerate(stacks):
+            mtb.align_stack(st["images"], st["levels"], st["noise_tol"], st["ref_idx"], workspace=wss[k],
+                            out=outs[k], stream=stream)
+
+    same = 0
+    for k, st in enumerate(stacks):  # per-level outputs too, outside the timed runs
+        r = mtb.align_stack(st["images"], st["levels"], st["noise_tol"], st["ref_idx"], level_outputs=True,
+                            workspace=wss[k], stream=stream)
+        same += int(torch.equal(r[0], batch.shifts[k]) and torch.equal(r[1], batch.level_errs[k]) and
+                    torch.equal(r[2], batch.level_shifts[k]))
+    torch.cuda.synchronize(dev)
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    Kp = max(1, min(K, 5))
+    p0.record(stream)
+    for _ in range(Kp):
+        plain()
+    p1.record(stream)
+    torch.cuda.synchronize(dev)
+    plain_ms = p0.elapsed_time(p1) / Kp
+    rec = {"stacks": count, "exposures": sum(sp.n for sp in specs), "pairs": sum(sp.pairs for sp in specs),
+           "aligned_mpix": round(pixels / 1e6, 1), "value": round(pixels / (ms / 1e3) / 1e6, 2), "unit": UNIT,
+           "ms_per_run": round(ms, 4), "runs": K,
+           "latency_ms": {"p50": round(_pct(step_ms, 0.50), 4), "p99": round(_pct(step_ms, 0.99), 4)},
+           "plain_value": round(pixels / (plain_ms / 1e3) / 1e6, 2), "plain_ms_per_run": round(plain_ms, 4),
+           "batch_vs_plain": round(plain_ms / ms, 3), "tile_shapes": cfg, "tune_s": round(t_tune, 2),
+           "status_ok": status == mtb.MTB_OK, "equal_plain_path": f"{same}/{count}",
+           "planted_shifts_recovered": f"{expected_ok}/{count} stacks",
+           "alg_GBps": round(abytes / (ms / 1e3) / 1e9, 1), "algorithmic_bytes_per_run": abytes}
+    if oracle_check:
+        t = time.perf_counter()
+        jobs = [(lambda k=k: (stacks[k]["images"].cpu().numpy(), specs[k].levels, specs[k].noise_tol,
+                              specs[k].ref)) for k in range(count)]
+        res = oracle_many(jobs, usable_cores())
+        eq = sum(np.array_equal(batch.shifts[k].cpu().numpy(), r["shifts"]) and
+                 np.array_equal(batch.level_errs[k].cpu().numpy().view(np.uint32), r["level_errs"]) and
+                 np.array_equal(batch.level_shifts[k].cpu().numpy(), r["level_shifts"])
+                 for k, r in enumerate(res))
+        rec["oracle_equal"] = f"{eq}/{count}"
+        rec["oracle_check"] = (f"shifts, per-level errors and per-level shifts of every stack vs the single-"
+                               f"threaded C oracle on {usable_cores()} host threads, {time.perf_counter() - t:.1f} s")
+    if clocks is not None:
+        rec["clocks"] = clocks
+    batch.close()
+    del stacks, wss, outs
+    torch.cuda.empty_cache()
+    return rec
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def run_gb300(args):
     import numpy as np
@@ -373,30 +512,43 @@ def run_gb300(args):
         mtb.search_shifts(n, w, h, L, spec.ref, wss[b], shifts[b], None, None, stream)
         ev[3].record(stream)
 
+    if args.profile_steps > 0:  # a short run for profilers: plain steps only, nothing timed or printed
+        for k in range(args.profile_steps):
+            step(k % B)
+        torch.cuda.synchronize(dev)
+        return
+
     for k in range(max(3, args.warmup)):
         step(k % B)
     torch.cuda.synchronize(dev)
 
     # throughput: K steps back to back between two events (an event between
     # two steps would end the overlap of one step's search with the next
-    # step's launches)
+    # step's launches); that region again and again, each time between a
+    # barrier and a synchronize, until the regions add up to min_timed_s
     K = args.steps
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     sampler = ClockSampler(dev.index if dev.index is not None else 0)
     sampler.start()
-    barrier(world)
-    torch.cuda.synchronize(dev)
-    t_wall = time.perf_counter()
-    t0.record(stream)
-    for k in range(K):
-        step(k % B)
-    t1.record(stream)
-    torch.cuda.synchronize(dev)
-    t_wall = time.perf_counter() - t_wall
-    barrier(world)
+    total_ms, t_wall, regions = 0.0, 0.0, 0
+    while True:
+        barrier(world)
+        torch.cuda.synchronize(dev)
+        tw = time.perf_counter()
+        t0.record(stream)
+        for k in range(K):
+            step(k % B)
+        t1.record(stream)
+        torch.cuda.synchronize(dev)
+        t_wall += time.perf_counter() - tw
+        barrier(world)
+        total_ms += max_over_ranks(t0.elapsed_time(t1), world, dev)
+        regions += 1
+        # every rank takes the same decision: the max over ranks of the wall time
+        if max_over_ranks(t_wall, world, dev) >= args.min_timed_s:
+            break
     clocks = sampler.stop()
-    total_ms = max_over_ranks(t0.elapsed_time(t1), world, dev)
-    ms_per_step = total_ms / K
+    ms_per_step = total_ms / (K * regions)
 
     # latency: max(LAT_STEPS, K) steps, each between its own two events, after
     # LAT_WARMUP more untimed ones
@@ -425,26 +577,33 @@ def run_gb300(args):
 
     # correctness of what was timed: every buffer's shifts vs the planted ones
     want = synth.expected_shifts(spec)
-    used = shifts[:min(B, max(3, args.warmup) + K)]
-    planted_ok = all(np.array_equal(s.cpu().numpy(), want) for s in used)
+    got = shifts[0].cpu().numpy()
+    same_all = all(torch.equal(s, shifts[0]) for s in shifts)
+    planted_ok = (f"{int((got == want).all(axis=1).sum())}/{n} exposures" +
+                  ("" if same_all else ", buffers disagree"))
 
     abytes = algorithmic_bytes(spec)
     peak, peak_kind = hbm_peak()
     step_bytes = sum(abytes.values())
-    # the dominant kernel is k_pyramid (the largest share of the step); its
-    # duration is the pyramid stage between CUDA events on the launching stream
-    # (k_clear before it is a single CTA clearing a few KB, overlapped by PDL)
+    # the dominant kernel is the stage with the largest share of the staged
+    # split; its duration is that stage between CUDA events on the launching
+    # stream (the pyramid stage's k_clear is a few-KB clear overlapped by PDL,
+    # the search stage's k_clear_search likewise)
     staged_total = sum(stage_ms.values())
-    achieved = abytes["pyramid"] / (stage_ms["pyramid"] / 1e3) / 1e9
-    roofline = {"bound": "hbm", "kernel": "k_pyramid", "achieved": round(achieved, 1), "peak": peak,
+    top = max(stage_ms, key=stage_ms.get)
+    achieved = abytes[top] / (stage_ms[top] / 1e3) / 1e9
+    call = {"pyramid": "mtb_build_pyramids", "bitmaps": "mtb_build_bitmaps", "search": "mtb_search_shifts"}
+    roofline = {"bound": "hbm", "kernel": STAGE_KERNEL[top], "achieved": round(achieved, 1), "peak": peak,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                "traffic": traffic_for("k_pyramid", spec.name), "algorithmic_bytes_per_launch": abytes["pyramid"],
-                "ms_per_launch": round(stage_ms["pyramid"], 5),
-                "share_of_staged_step": round(stage_ms["pyramid"] / staged_total, 3),
-                "duration_source": f"CUDA events around mtb_build_pyramids, {len(sev)} staged steps after the "
+                "traffic": traffic_for(STAGE_KERNEL[top], spec.name), "algorithmic_bytes_per_launch": abytes[top],
+                "ms_per_launch": round(stage_ms[top], 5),
+                "share_of_staged_step": round(stage_ms[top] / staged_total, 3),
+                "duration_source": f"CUDA events around {call[top]}, {len(sev)} staged steps after the "
                                    f"timed region, same buffers and stream"}
-    stages = {k: {"ms": round(v, 5), "alg_GBps": round(abytes[k] / (v / 1e3) / 1e9, 1),
-                  "frac_of_peak": round(abytes[k] / (v / 1e3) / 1e9 / peak, 4)} for k, v in stage_ms.items()}
+    stages = {k: {"kernel": STAGE_KERNEL[k], "ms": round(v, 5), "share": round(v / staged_total, 3),
+                  "alg_GBps": round(abytes[k] / (v / 1e3) / 1e9, 1),
+                  "frac_of_peak": round(abytes[k] / (v / 1e3) / 1e9 / peak, 4),
+                  "traffic": traffic_for(STAGE_KERNEL[k], spec.name)} for k, v in stage_ms.items()}
 
     # ---- end to end through the host-buffer entry point ----
     e2e = None
@@ -465,21 +624,32 @@ def run_gb300(args):
         e1.record(stream)
         torch.cuda.synchronize(dev)
         e_ms = max_over_ranks(e0.elapsed_time(e1) / Ke, world, dev)
-        planted_ok = planted_ok and np.array_equal(out.numpy(), want)
+        e2e_same = np.array_equal(out.numpy(), got)
         e2e = {"value": round(world * spec.aligned_pixels / (e_ms / 1e3) / 1e6, 2), "unit": UNIT,
                "ms_per_step": round(e_ms, 4), "h2d_bytes_per_step": int(host.numel()),
-               "d2h_bytes_per_step": int(out.numel() * out.element_size()), "steps": Ke}
+               "d2h_bytes_per_step": int(out.numel() * out.element_size()), "steps": Ke,
+               "shifts_equal_device_path": bool(e2e_same)}
 
     cpu = cpu_threaded = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         res = oracle_rate(images.cpu().numpy(), spec)
         gpu_match = all(np.array_equal(s.cpu().numpy(), res["result"]["shifts"]) for s in shifts)
+        g_s, g_e, g_l = mtb.align_stack(images, L, spec.noise_tol, spec.ref, level_outputs=True, workspace=wss[0],
+                                        stream=stream)
+        levels_match = (np.array_equal(g_e.cpu().numpy().view(np.uint32), res["result"]["level_errs"]) and
+                        np.array_equal(g_l.cpu().numpy(), res["result"]["level_shifts"]))
         cpu = {k: v for k, v in res.items() if k != "result"}
         cpu["value"] = round(cpu["value"], 3)
         cpu["gpu_shifts_equal_oracle"] = bool(gpu_match)
+        cpu["gpu_level_errors_and_shifts_equal_oracle"] = bool(levels_match)
         if args.cpu_threads != 1:
             nthr = args.cpu_threads if args.cpu_threads > 0 else len(os.sched_getaffinity(0))
             cpu_threaded = oracle_rate_threaded(images.cpu().numpy(), spec, nthr)
+
+    batch = None
+    if rank == 0 and world == 1 and args.batch_count > 0:
+        batch = batch_record(args.batch_count, dev, stream, args.warmup, 5,
+                             oracle_check=not args.no_cpu_baseline)
 
     if rank == 0:
         line = {
@@ -499,9 +669,11 @@ def run_gb300(args):
             "cpu_baseline": cpu,
             "cpu_baseline_threaded": cpu_threaded,
             "e2e": e2e,
-            "gpu_launches": K * kernels_per_step(spec),
+            "batch": batch,
+            "gpu_launches": K * regions * kernels_per_step(spec),
             "clocks": clocks,
-            "planted_shifts_recovered": bool(planted_ok),
+            "planted_shifts_recovered": planted_ok,
+            "timed_regions": regions,
             "wall_s_timed_region": round(t_wall, 4),
         }
         print(json.dumps(line), flush=True)
@@ -513,39 +685,44 @@ def run_gb300(args):
 
 # ----------------------------------------------------------------------------- reference arm
 def run_reference(args):
-    """The oracle as it stands, on the host cores, on the same workload and metric.
-    A step aligns one exposure pair of the stack (the reference and the next
-    exposure, both pyramids built) -- the unit of the metric."""
+    """The oracle as it stands, on the host cores, on the same workload, metric
+    and unit as the GPU arm: a step aligns the whole stack (every exposure's
+    pyramid built, every pair searched), on the same input bytes the GPU arm
+    aligns (the stack is generated on the GPU when there is one, as the GPU arm
+    does, and copied to the host).  If K + W whole stacks would take more than
+    about 150 s, every exposure is cropped to its first rows, and the line says
+    so."""
     world, rank, _ = dist_env()
     if rank != 0:
         return
     import numpy as np
+    import torch
 
     import oracle
     from paper_2007_06483_gb300 import synth
 
     spec = workload(args.workload)
-    images = synth.make_stack(spec).numpy()
-    other = (spec.ref + 1) % spec.n
-    pair = np.ascontiguousarray(images[[spec.ref, other]])
+    gen_dev = "cuda" if torch.cuda.is_available() else "cpu"
+    images = synth.make_stack(spec, gen_dev).cpu().numpy()
     t = time.perf_counter()
-    oracle.align_stack(pair, spec.levels, spec.noise_tol, 0)
+    oracle.align_stack(images, spec.levels, spec.noise_tol, spec.ref)
     one = time.perf_counter() - t
-    # keep the whole run within about three minutes: crop rows if a step is too slow
     budget = 150.0
     rows = spec.h
     if one * (args.steps + args.warmup) > budget:
         rows = max(1 << (spec.levels - 1), int(spec.h * budget / (one * (args.steps + args.warmup))))
-        pair = np.ascontiguousarray(pair[:, :rows])
+        images = np.ascontiguousarray(images[:, :rows])
     for _ in range(args.warmup):
-        oracle.align_stack(pair, spec.levels, spec.noise_tol, 0)
+        oracle.align_stack(images, spec.levels, spec.noise_tol, spec.ref)
     t = time.perf_counter()
     for _ in range(args.steps):
-        oracle.align_stack(pair, spec.levels, spec.noise_tol, 0)
+        oracle.align_stack(images, spec.levels, spec.noise_tol, spec.ref)
     dt = (time.perf_counter() - t) / args.steps
-    px = spec.w * rows
+    px = spec.pairs * spec.w * rows
     value = px / dt / 1e6
-    sample = f"one {spec.w}x{rows} exposure pair of {spec.name} per step, single-threaded C oracle"
+    crop = "" if rows == spec.h else f", cropped to the first {rows} of {spec.h} rows"
+    sample = (f"the whole {spec.name} stack ({spec.pairs} pairs) per step{crop}, single-threaded C oracle, "
+              f"inputs generated on {gen_dev} as the GPU arm's")
     line = {
         "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 3), "higher_is_better": True,
@@ -563,89 +740,41 @@ def run_reference(args):
 def run_batch(args):
     """Uneven stacks (synth.batch_specs) in one persistent graph-captured launch,
     after the autotuner picked its tile shapes; the same stacks through the
-    plain per-stack path for comparison.  A step aligns every stack once."""
-    import numpy as np
+    plain per-stack path for comparison, and every stack checked against the
+    plain path and the oracle.  A step aligns every stack once."""
     import torch
 
     from paper_2007_06483_gb300 import build as cuda_build
 
     cuda_build.build()
-    import paper_2007_06483_gb300 as mtb
-    from paper_2007_06483_gb300 import synth
 
     count = int(args.workload[len("batch"):] or 256)
-    specs = synth.batch_specs(count)
     dev = torch.device("cuda", torch.cuda.current_device())
-    stacks = [{"images": synth.make_stack(sp, dev), "levels": sp.levels, "noise_tol": sp.noise_tol,
-               "ref_idx": sp.ref} for sp in specs]
-    pixels = sum(sp.aligned_pixels for sp in specs)
-    abytes = sum(sum(algorithmic_bytes(sp).values()) for sp in specs)
     stream = torch.cuda.current_stream(dev)
-    batch = mtb.Batch(stacks, level_outputs=False)
-    batch.tune(reps=2, stream=stream)
-    cfg = batch.config()
-    for _ in range(max(3, args.warmup)):
-        batch.run(stream)
-    torch.cuda.synchronize(dev)
-    K = args.steps
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(K)]
-    sampler = ClockSampler(dev.index or 0)
-    sampler.start()
-    for k in range(K):
-        evs[k][0].record(stream)
-        batch.run(stream)
-        evs[k][1].record(stream)
-    torch.cuda.synchronize(dev)
-    clocks = sampler.stop()
-    assert batch.status() == mtb.MTB_OK
-    step_ms = [e[0].elapsed_time(e[1]) for e in evs]
-    ms = evs[0][0].elapsed_time(evs[-1][1]) / K
-    expected_ok = sum(np.array_equal(batch.shifts[k].cpu().numpy(), synth.expected_shifts(sp))
-                      for k, sp in enumerate(specs))
-
-    # the same stacks through the plain path, one stack after the other
-    wss = [mtb.new_workspace(sp.n, sp.w, sp.h, sp.levels, device=dev) for sp in specs]
-    outs = [torch.empty((sp.n, 2), dtype=torch.int32, device=dev) for sp in specs]
-
-    def plain():
-        for k, st in enumerate(stacks):
-            mtb.align_stack(st["images"], st["levels"], st["noise_tol"], st["ref_idx"], workspace=wss[k],
-                            out=outs[k], stream=stream)
-
-    plain()
-    torch.cuda.synchronize(dev)
-    same = all(torch.equal(outs[k], batch.shifts[k]) for k in range(count))
-    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    Kp = max(1, min(K, 5))
-    p0.record(stream)
-    for _ in range(Kp):
-        plain()
-    p1.record(stream)
-    torch.cuda.synchronize(dev)
-    plain_ms = p0.elapsed_time(p1) / Kp
+    rec = batch_record(count, dev, stream, args.warmup, args.steps, oracle_check=not args.no_cpu_baseline,
+                       sampler=ClockSampler(dev.index or 0))
     peak, peak_kind = hbm_peak()
-    achieved = abytes / (ms / 1e3) / 1e9
+    achieved = rec["alg_GBps"]
     line = {
-        "metric": METRIC + " (batched)", "value": round(pixels / (ms / 1e3) / 1e6, 2), "unit": UNIT, "n_gpus": 1,
-        "steps": K, "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": f"batch{count}", "stacks": count, "exposures": sum(sp.n for sp in specs),
-                   "pairs": sum(sp.pairs for sp in specs), "aligned_mpix": round(pixels / 1e6, 1),
-                   "tile_shapes": cfg, "l2": "inputs of the batch far exceed L2"},
-        "plain_path": {"value": round(pixels / (plain_ms / 1e3) / 1e6, 2), "ms_per_step": round(plain_ms, 4),
-                       "same_shifts_as_batch": bool(same)},
-        "batch_vs_plain": round(plain_ms / ms, 3),
-        "latency_ms": {"p50": round(_pct(step_ms, 0.50), 4), "p99": round(_pct(step_ms, 0.99), 4),
-                       "runs": len(step_ms)},
-        "hbm_gbs": round(achieved, 1),
-        "roofline": {"bound": "hbm", "kernel": "k_engine<batch> (after k_engine_clear)", "achieved": round(achieved, 1),
+        "metric": METRIC + " (batched)", "value": rec["value"], "unit": UNIT, "n_gpus": 1,
+        "steps": rec["runs"], "warmup": args.warmup, "ms_per_step": rec["ms_per_run"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": f"batch{count}", "stacks": count, "exposures": rec["exposures"],
+                   "pairs": rec["pairs"], "aligned_mpix": rec["aligned_mpix"], "tile_shapes": rec["tile_shapes"],
+                   "l2": "inputs of the batch far exceed L2"},
+        "plain_path": {"value": rec["plain_value"], "ms_per_step": rec["plain_ms_per_run"],
+                       "equal_plain_path": rec["equal_plain_path"]},
+        "batch_vs_plain": rec["batch_vs_plain"],
+        "oracle_equal": rec.get("oracle_equal"), "oracle_check": rec.get("oracle_check"),
+        "latency_ms": rec["latency_ms"],
+        "hbm_gbs": achieved,
+        "roofline": {"bound": "hbm", "kernel": "k_engine<batch> (after k_engine_clear)", "achieved": achieved,
                      "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                     "traffic": None, "algorithmic_bytes_per_launch": abytes},
-        "gpu_launches": 2 * K, "clocks": clocks,
-        "planted_shifts_recovered": f"{expected_ok}/{count} stacks",
+                     "traffic": None, "algorithmic_bytes_per_launch": rec["algorithmic_bytes_per_run"]},
+        "gpu_launches": 2 * rec["runs"], "clocks": rec.get("clocks"),
+        "planted_shifts_recovered": rec["planted_shifts_recovered"],
     }
     print(json.dumps(line), flush=True)
-    batch.close()
 
 
 # ----------------------------------------------------------------------------- serving
@@ -702,6 +831,14 @@ def run_serve(args):
         resident.append(d)
         alone.append(out.cpu())
         planted += int(np.array_equal(alone[-1].numpy(), synth.expected_shifts(sp)))
+    # every job's answer from the oracle, on every usable host core (outside the timed sweep)
+    t_orc = time.perf_counter()
+    orc = None
+    if not args.no_cpu_baseline:
+        res = oracle_many([(lambda h=h, sp=sp: (h.numpy(), sp.levels, sp.noise_tol, sp.ref))
+                           for h, sp in zip(pool, specs)], usable_cores())
+        orc = [torch.from_numpy(r["shifts"].astype(np.int32)) for r in res]
+    t_orc = time.perf_counter() - t_orc
     # the plain path on the same jobs, inputs already in HBM, for comparison
     ws = mtb.new_workspace(specs[0].n, specs[0].w, specs[0].h, specs[0].levels, device=dev)
     outp = torch.empty((specs[0].n, 2), dtype=torch.int32, device=dev)
@@ -757,7 +894,7 @@ def run_serve(args):
             th = threading.Thread(target=submitter)
             th.start()
             lat, queue, done_at = [], [], []
-            same = 0
+            same = orc_same = 0
             for i in range(count):
                 while ids[i] is None:
                     time.sleep(0.0002)
@@ -769,6 +906,7 @@ def run_serve(args):
                 queue.append(q_ms + slip[i] * 1e3)
                 done_at.append(sched[i] + l_ms / 1e3)
                 same += int(torch.equal(shifts, alone[picks[i]]))
+                orc_same += int(orc is not None and torch.equal(shifts, orc[picks[i]]))
             th.join()
             st = srv.stats()
             span = max(done_at)
@@ -781,6 +919,7 @@ def run_serve(args):
                 "queue_p50_ms": round(_pct(queue, 0.50), 3), "queue_p99_ms": round(_pct(queue, 0.99), 3),
                 "submit_slip_p99_ms": round(_pct(slip, 0.99) * 1e3, 3),
                 "same_as_alone": f"{same}/{count}",
+                "oracle_equal": f"{orc_same}/{count}" if orc is not None else None,
             })
         clocks = sampler.stop()
         st = srv.stats()
@@ -805,6 +944,11 @@ def run_serve(args):
                      "unit": "GB/s", "frac": round(best["h2d_gbs"] / link_gbs, 4), "traffic": None},
         "server_stats": st,
         "results_same_alone_and_in_mix": bool(all_same),
+        "alone_equal_oracle": (f"{sum(torch.equal(a, o) for a, o in zip(alone, orc))}/{len(alone)}"
+                               if orc is not None else None),
+        "oracle_check": (f"every served job's shifts vs the single-threaded C oracle's answer for its pool job "
+                         f"({len(pool)} jobs on {usable_cores()} host threads, {t_orc:.1f} s, before the sweep)"
+                         if orc is not None else None),
         "planted_shifts_recovered": f"{planted}/{len(specs)} jobs",
         "gpu_launches": kernels_per_step(sp0) * sum(r["jobs"] for r in results), "clocks": clocks,
     }

@@ -307,7 +307,10 @@ void mtb_batch_destroy(mtb_batch_t *batch);
  * - A stack whose mtb_workspace_bytes() exceeds MTB_NOALLOC_SCRATCH_BYTES is
  *   rejected with MTB_ERR_INVALID_ARG before anything is enqueued.
  * - The first call on a device looks the array's address up (cudaGetSymbolAddress)
- *   with that device current; make that first call before any stream capture.
+ *   with that device current and keeps it for that device's context; a call
+ *   that finds another context current (after cudaDeviceReset) looks it up
+ *   again.  Make the first call, and the first call after a reset, before any
+ *   stream capture.
  * - All calls on a device share the array.  Calls whose GPU work overlaps (other
  *   streams, other host threads) race and give wrong results: order them. */
 int mtb_align_stack_noalloc(const uint8_t *images, int n_exposures, int w, int h, int levels,

@@ -216,6 +216,34 @@ int enqueue_banded(const uint8_t *host_images, uint8_t *d_img, const mtb_layout_
 
 bool misaligned(const void *p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) != 0; }
 
+// Whether the byte ranges [a, a + na) and [b, b + nb) share a byte (a null
+// pointer or an empty range shares none).
+bool overlaps(const void *a, size_t na, const void *b, size_t nb) {
+    if (!a || !b || na == 0 || nb == 0) return false;
+    const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+    return x < y + nb && y < x + na;
+}
+
+// The outputs of an alignment call must not overlap the images, and a caller
+// workspace none of them: the kernels write the workspace and the outputs
+// while they read the images.
+bool buffers_alias(const uint8_t *images, int n, int w, int h, int levels, const void *shifts_out,
+                   const void *level_errs_out, const void *level_shifts_out, const void *workspace,
+                   size_t workspace_bytes) {
+    const size_t img = (size_t)n * w * h * 3;
+    const size_t sh = (size_t)n * 2 * sizeof(int32_t), le = (size_t)n * levels * 9 * sizeof(uint32_t),
+                 ls = (size_t)n * levels * 2 * sizeof(int32_t);
+    const void *outs[3] = {shifts_out, level_errs_out, level_shifts_out};
+    const size_t sizes[3] = {sh, le, ls};
+    for (int k = 0; k < 3; ++k) {
+        if (overlaps(outs[k], sizes[k], images, img) || overlaps(outs[k], sizes[k], workspace, workspace_bytes))
+            return true;
+        for (int j = k + 1; j < 3; ++j)
+            if (overlaps(outs[k], sizes[k], outs[j], sizes[j])) return true;
+    }
+    return overlaps(workspace, workspace_bytes, images, img);
+}
+
 // Caller workspace if given (checked), else a stream-ordered allocation.
 int acquire(void *given, size_t given_bytes, size_t need, cudaStream_t s, uint8_t **ws, bool *owned) {
     *owned = false;
@@ -287,6 +315,9 @@ int mtb_align_stack_ex(const uint8_t *images, int n_exposures, int w, int h, int
     int rc = check_stack_args(n_exposures, w, h, levels, noise_tol, ref_idx);
     if (rc != MTB_OK) return rc;
     if (!images || !shifts_out || misaligned(images, 16)) return MTB_ERR_INVALID_ARG;
+    if (buffers_alias(images, n_exposures, w, h, levels, shifts_out, level_errs_out, level_shifts_out, workspace,
+                      workspace_bytes))
+        return MTB_ERR_INVALID_ARG;
     mtb_layout_t L;
     compute_layout(n_exposures, w, h, levels, &L);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -304,6 +335,9 @@ int mtb_align_stack_chain(const uint8_t *images, int n_exposures, int w, int h, 
     int rc = check_stack_args(n_exposures, w, h, levels, noise_tol, ref_idx);
     if (rc != MTB_OK) return rc;
     if (!images || !shifts_out || misaligned(images, 16)) return MTB_ERR_INVALID_ARG;
+    if (buffers_alias(images, n_exposures, w, h, levels, shifts_out, level_errs_out, level_shifts_out, workspace,
+                      workspace_bytes))
+        return MTB_ERR_INVALID_ARG;
     mtb_layout_t L;
     compute_layout(n_exposures, w, h, levels, &L);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -329,6 +363,7 @@ int mtb_build_pyramids(const uint8_t *images, int n_exposures, int w, int h, int
     if (!images || misaligned(images, 16) || !workspace || workspace_bytes < L.total_bytes ||
         misaligned(workspace, 256))
         return MTB_ERR_INVALID_ARG;
+    if (overlaps(workspace, workspace_bytes, images, (size_t)n_exposures * w * h * 3)) return MTB_ERR_INVALID_ARG;
     return stage_pyramid(images, L, static_cast<uint8_t *>(workspace), static_cast<cudaStream_t>(stream));
 }
 
@@ -351,6 +386,9 @@ int mtb_search_shifts(int n_exposures, int w, int h, int levels, int ref_idx, vo
     if (rc != MTB_OK) return rc;
     if (ref_idx < 0 || ref_idx >= n_exposures) return MTB_ERR_INVALID_ARG;
     if (!workspace || workspace_bytes < L.total_bytes || misaligned(workspace, 256)) return MTB_ERR_INVALID_ARG;
+    if (buffers_alias(nullptr, n_exposures, w, h, levels, shifts_out, level_errs_out, level_shifts_out, workspace,
+                      workspace_bytes))
+        return MTB_ERR_INVALID_ARG;
     return cuda_status(launch_search(L, ref_idx, static_cast<uint8_t *>(workspace), shifts_out, level_errs_out,
                                      level_shifts_out, static_cast<cudaStream_t>(stream), false));
 }
@@ -460,6 +498,14 @@ int mtb_align_quadrants(const uint8_t *images, int n_exposures, int w, int h, in
     mtb_layout_t Lq;
     size_t stride, wso, so, total;
     quadrant_layout(n_exposures, w, h, levels, &Lq, &stride, &wso, &so, &total);
+    {
+        const size_t img = (size_t)n_exposures * w * h * 3, qs = (size_t)n_exposures * 4 * 2 * sizeof(int32_t),
+                     fl = (size_t)n_exposures * sizeof(int32_t);
+        if (overlaps(workspace, workspace_bytes, images, img) || overlaps(quad_shifts_out, qs, images, img) ||
+            overlaps(quad_shifts_out, qs, workspace, workspace_bytes) || overlaps(flags_out, fl, images, img) ||
+            overlaps(flags_out, fl, workspace, workspace_bytes) || overlaps(flags_out, fl, quad_shifts_out, qs))
+            return MTB_ERR_INVALID_ARG;
+    }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     uint8_t *base = nullptr;
     bool owned = false;

@@ -35,8 +35,15 @@ __global__ void __launch_bounds__(kBitThreads, 5)
 k_bitmaps(const mtb_layout_t L, uint8_t *__restrict__ ws, int tol, int deep_ctas) {
     __shared__ uint32_t s_hist[256];
     __shared__ int s_med;
-    pdl_trigger();
+    // Wait before letting the search launch.  The search of the same call
+    // starts without waiting for this grid (it polls the bit_done counters),
+    // and it reads words that the call's clearing kernel zeroes: its queue
+    // head, those counters and the status word.  This wait returns only once
+    // the pyramid pass has completed, and every pyramid CTA itself waited for
+    // the clearing kernel, so a search that launches after this trigger sees
+    // the cleared words, even on a workspace a previous call left dirty.
     pdl_wait();  // gray planes and medians come from the pyramid pass
+    pdl_trigger();
     if ((int)blockIdx.x < deep_ctas) {
         deep_levels(L, ws, tol, blockIdx.x, s_hist, &s_med);
         return;

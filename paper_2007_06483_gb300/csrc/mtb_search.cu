@@ -43,7 +43,10 @@ namespace {
 // clearing was done by the pyramid stage; the search then starts while the
 // bitmaps are still being packed, and every item waits for the planes it reads
 // (their completion counters, acquired; weak loads afterwards) instead of for
-// the whole previous launch.
+// the whole previous launch.  Its words that the call's clearing kernel zeroes
+// (queue head, counters, status) are clear by the time it launches: the bitmap
+// pass lets it launch only after its own wait on the pyramid pass, which
+// completes only after the clearing kernel.
 template <bool kOverlap>
 // 3 CTAs per SM: 80 registers and no spills.  At 4 (64 registers) the item
 // functions spilled 124 bytes and the 4000x3000x3 one-call step took 85.1 us

@@ -180,3 +180,29 @@ def test_output_checks(bad):
     with pytest.raises(ValueError, match="workspace"):
         mtb._workspace(torch.empty(64, dtype=torch.uint8, device="meta"), dev)
     assert mtb._workspace(torch.empty(64, dtype=torch.int32), dev)[1] == 256
+
+
+def test_aliasing_buffers_rejected_on_host(mtb_lib):
+    """A workspace or an output that shares bytes with the images (or with each
+    other) is refused before anything is enqueued: the kernels would write it
+    while they read the images."""
+    lib = mtb_lib.lib()
+    n, w, h, L = 2, 64, 64, 3
+    img = 1 << 30
+    img_bytes = n * w * h * 3
+    nbytes = mtb_lib.workspace_bytes(n, w, h, L)
+    ws_far = 1 << 32
+    bad = mtb_lib.MTB_ERR_INVALID_ARG
+    # workspace over the images' last bytes
+    assert lib.mtb_align_stack_ex(img, n, w, h, L, 4, 0, 1 << 20, None, None, img + img_bytes - 256 * 1, nbytes,
+                                  None) == bad
+    # shifts inside the images, inside the workspace; level outputs over the shifts
+    assert lib.mtb_align_stack_ex(img, n, w, h, L, 4, 0, img + 64, None, None, ws_far, nbytes, None) == bad
+    assert lib.mtb_align_stack_ex(img, n, w, h, L, 4, 0, ws_far + 4096, None, None, ws_far, nbytes, None) == bad
+    assert lib.mtb_align_stack_ex(img, n, w, h, L, 4, 0, 1 << 20, (1 << 20) + 8, None, ws_far, nbytes, None) == bad
+    assert lib.mtb_align_stack_chain(img, n, w, h, L, 4, 0, 1 << 20, None, None, img, nbytes, None) == bad
+    assert lib.mtb_build_pyramids(img, n, w, h, L, img + 256, nbytes, None) == bad
+    assert lib.mtb_search_shifts(n, w, h, L, 0, ws_far, nbytes, ws_far + 512, None, None, None) == bad
+    qbytes = lib.mtb_quadrant_workspace_bytes(n, w, h, L - 1)
+    assert lib.mtb_align_quadrants(img, n, w, h, L - 1, 4, 0, 1, 1 << 20, (1 << 20) + 16, ws_far, qbytes,
+                                   None) == bad

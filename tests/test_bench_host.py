@@ -38,3 +38,26 @@ def test_threaded_oracle_baseline_small_stack():
     r = bench.oracle_rate_threaded(images, spec, 2, budget_s=0.3)
     assert r["cores"] == 2 and r["kind"] == "oracle" and r["value"] > 0
     assert "2 threads" in r["sample"]
+
+
+def test_oracle_many_equals_one_by_one():
+    import oracle
+
+    specs = [synth.small_spec(60 + k, 96 + 16 * k, 64, n=3, levels=3, ref=1) for k in range(4)]
+    stacks = [synth.make_stack(sp).numpy() for sp in specs]
+    jobs = [(lambda k=k: (stacks[k], specs[k].levels, specs[k].noise_tol, specs[k].ref)) for k in range(4)]
+    many = bench.oracle_many(jobs, 3)
+    for k, r in enumerate(many):
+        one = oracle.align_stack(stacks[k], specs[k].levels, specs[k].noise_tol, specs[k].ref)
+        for key in ("shifts", "level_errs", "level_shifts"):
+            assert np.array_equal(r[key], one[key]), (k, key)
+
+
+def test_reference_arm_times_whole_stacks(capsys):
+    import json
+
+    bench.main(["--impl", "reference", "--workload", "pair640x480", "--steps", "2", "--warmup", "1"])
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["config"]["workload"] == "pair640x480"
+    assert line["unit"] == "MPix/s" and line["value"] > 0 and line["e2e"]["value"] == line["value"]
+    assert "whole pair640x480 stack" in line["cpu_baseline"]["sample"]

@@ -202,3 +202,25 @@ def test_binding_rejects_outputs_it_could_overrun(mtb_lib):
                                                                                device="cuda"))
     with pytest.raises(ValueError, match="workspace must be"):
         mtb_lib.align_stack(imgs, 3, workspace=ws[::2])
+
+
+@pytest.mark.parametrize("w,h,n,levels,ref", [(64, 48, 3, 4, 1), (640, 480, 4, 6, 2), (2000, 1500, 3, 7, 1)])
+def test_dirty_workspace_one_call(mtb_lib, oracle_mod, w, h, n, levels, ref):
+    """The one-call path on a workspace whose bookkeeping a previous user left
+    full of large values (queue head, completion counters, status word, error
+    sums): the call's own clearing must come before the search reads any of
+    them, also for stacks small enough that every kernel of the call is
+    resident at once.  Two different stacks run back to back on it, each
+    compared with the oracle."""
+    lay = mtb_lib.layout(n, w, h, levels)
+    ws = mtb_lib.new_workspace(n, w, h, levels)
+    stacks = [_natural(900 + k, w, h, n, levels, ref=ref, shift_range=7) for k in range(2)]
+    wants = [oracle_mod.align_stack(s.cpu().numpy(), levels, 4, ref) for s in stacks]
+    for rep in range(3):
+        ws[lay.hist_offset:].fill_(0x7F)  # every bookkeeping word 0x7f7f7f7f
+        for s, want in zip(stacks, wants):
+            shifts = torch.full((n, 2), -999, dtype=torch.int32, device="cuda")
+            mtb_lib.align_stack(s, levels, 4, ref, workspace=ws, out=shifts)
+            torch.cuda.synchronize()
+            assert mtb_lib.get_last_status() == mtb_lib.MTB_OK
+            assert np.array_equal(shifts.cpu().numpy(), want["shifts"]), (rep, shifts.cpu().numpy(), want["shifts"])

@@ -58,3 +58,62 @@ def test_noalloc_rejects_stacks_beyond_its_scratch(mtb_lib):
     assert mtb_lib.workspace_bytes(2, w, h, 8) > NOALLOC_SCRATCH_BYTES
     rc = fn(imgs.data_ptr(), 2, w, h, 8, 4, 0, out.data_ptr(), None, None, None)
     assert rc == mtb_lib.MTB_ERR_INVALID_ARG
+
+
+class _DefaultPool:
+    """The device's default stream-ordered memory pool, read through the driver
+    (libcuda): its used-memory high watermark shows any cudaMallocAsync made
+    between two readings, also one freed again before the second."""
+
+    USED_MEM_CURRENT, USED_MEM_HIGH = 7, 8  # CU_MEMPOOL_ATTR_*
+
+    def __init__(self, index: int):
+        self.cu = ctypes.CDLL("libcuda.so.1")
+        dev = ctypes.c_int()
+        assert self.cu.cuDeviceGet(ctypes.byref(dev), index) == 0
+        self.pool = ctypes.c_void_p()
+        assert self.cu.cuDeviceGetDefaultMemPool(ctypes.byref(self.pool), dev) == 0
+
+    def get(self, attr: int) -> int:
+        v = ctypes.c_uint64()
+        assert self.cu.cuMemPoolGetAttribute(self.pool, attr, ctypes.byref(v)) == 0
+        return v.value
+
+    def reset_high(self):
+        zero = ctypes.c_uint64(0)  # the high watermark may only be set to 0, which resets it
+        assert self.cu.cuMemPoolSetAttribute(self.pool, self.USED_MEM_HIGH, ctypes.byref(zero)) == 0
+
+
+def test_noalloc_allocates_nothing(mtb_lib):
+    """What the entry point is for: once set up, a call makes no device
+    allocation -- none through the stream-ordered pool (whose high watermark
+    would show even an allocation freed within the call) and none through
+    torch's allocator."""
+    fn = _c_entry(mtb_lib)
+    spec = synth.small_spec(43, 960, 540, n=3, levels=5, shift_range=12, ref=1)
+    imgs = synth.make_stack(spec, "cuda")
+    n, L = spec.n, spec.levels
+    outs = [torch.empty((n, 2), dtype=torch.int32, device="cuda"),
+            torch.empty((n, L, 9), dtype=torch.int32, device="cuda"),
+            torch.empty((n, L, 2), dtype=torch.int32, device="cuda")]
+    stream = torch.cuda.current_stream().cuda_stream
+
+    def call():
+        return fn(imgs.data_ptr(), n, spec.w, spec.h, L, spec.noise_tol, spec.ref, outs[0].data_ptr(),
+                  outs[1].data_ptr(), outs[2].data_ptr(), stream)
+
+    assert call() == 0  # set-up: the scratch address is looked up here
+    torch.cuda.synchronize()
+    want = mtb_lib.align_stack(imgs, L, spec.noise_tol, spec.ref)  # may use the pool itself
+    torch.cuda.synchronize()
+    pool = _DefaultPool(torch.cuda.current_device())
+    used = pool.get(pool.USED_MEM_CURRENT)
+    pool.reset_high()
+    torch.cuda.reset_peak_memory_stats()
+    torch_before = torch.cuda.memory_allocated()
+    for _ in range(2):
+        assert call() == 0
+    torch.cuda.synchronize()
+    assert pool.get(pool.USED_MEM_HIGH) <= used, "the no-alloc call allocated from the stream-ordered pool"
+    assert torch.cuda.max_memory_allocated() == torch_before, "device memory was allocated during the call"
+    assert torch.equal(outs[0], want)
