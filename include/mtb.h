@@ -72,7 +72,8 @@ extern "C" {
  *                e * gray_exposure_stride for exposure e
  *   bit plane    uint32 pairs (tb word, eb word) [height[l]][bits_pitch[l]], at
  *                bits_offset[l] + e * bits_exposure_stride; bit b of word q of a
- *                row is pixel 32*q + b; bits at x >= width[l] are 0
+ *                row is pixel 32*q + b; bits at x >= width[l] are 0, and the
+ *                last 2 words of every row hold no pixel
  *   hist         uint32 [n][levels][256]
  *   median       int32  [n][levels]
  *   errs         uint32 [n][levels][9]   (candidate errors, reference row 0)

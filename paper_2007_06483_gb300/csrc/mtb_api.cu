@@ -54,7 +54,10 @@ int compute_layout(int n, int w, int h, int levels, mtb_layout_t *L) {
         L->width[l] = w >> l;
         L->height[l] = h >> l;
         L->gray_pitch[l] = (int32_t)align_up((size_t)L->width[l], 32);
-        L->bits_pitch[l] = (int32_t)align_up(((size_t)L->width[l] + 31) / 32, 2);
+        // at least 2 zero words end every row: a run of rows copied as it lies
+        // has zeros on both sides of each row's data (the search reads past
+        // the row ends without checks)
+        L->bits_pitch[l] = (int32_t)align_up(((size_t)L->width[l] + 31) / 32 + 2, 2);
         L->gray_offset[l] = per_exp;
         per_exp += align_up((size_t)L->gray_pitch[l] * L->height[l], 256);
     }

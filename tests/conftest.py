@@ -48,3 +48,19 @@ def mtb_lib():
 
     mtb.lib()
     return mtb
+
+
+@pytest.fixture(params=["auto", "staged", "items"])
+def search_kernel(request, monkeypatch):
+    """The shift search has two kernels, the staged cluster kernel and the item
+    kernel.  The library picks one by stack size and call mode, and
+    MTB_SEARCH_ITEMS (read at every launch) forces one: 0 the staged kernel, 1
+    the item kernel.  The parity tests run under the library's choice and under
+    each kernel forced."""
+    if request.param == "staged":
+        monkeypatch.setenv("MTB_SEARCH_ITEMS", "0")
+    elif request.param == "items":
+        monkeypatch.setenv("MTB_SEARCH_ITEMS", "1")
+    else:
+        monkeypatch.delenv("MTB_SEARCH_ITEMS", raising=False)
+    return request.param

@@ -29,7 +29,7 @@ CHAIN = [(96, 80, 2, 4, 1), (160, 120, 5, 5, 2), (333, 222, 4, 5, 0), (640, 480,
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("w,h,n,levels,ref", CHAIN)
-def test_chain_matches_oracle(mtb_lib, oracle_mod, w, h, n, levels, ref):
+def test_chain_matches_oracle(search_kernel, mtb_lib, oracle_mod, w, h, n, levels, ref):
     spec = synth.small_spec(900 + w, w, h, n=n, levels=levels, shift_range=min(6, (1 << levels) - 1), ref=ref)
     imgs = synth.make_stack(spec, "cuda")
     shifts, errs, lsh = mtb_lib.align_stack_chain(imgs, levels, 4, ref, level_outputs=True)
@@ -43,7 +43,7 @@ def test_chain_matches_oracle(mtb_lib, oracle_mod, w, h, n, levels, ref):
 
 
 @pytest.mark.gpu
-def test_chain_full_size(mtb_lib, oracle_mod):
+def test_chain_full_size(search_kernel, mtb_lib, oracle_mod):
     spec = synth.STACK_12MP
     imgs = synth.make_stack(spec, "cuda")
     shifts = mtb_lib.align_stack_chain(imgs, spec.levels, spec.noise_tol, spec.ref)

@@ -48,19 +48,19 @@ SHAPES = [
 
 
 @pytest.mark.parametrize("w,h,levels,n,ref", SHAPES)
-def test_shapes_natural(mtb_lib, oracle_mod, w, h, levels, n, ref):
+def test_shapes_natural(search_kernel, mtb_lib, oracle_mod, w, h, levels, n, ref):
     imgs = _natural(100 + w + 7 * h, w, h, n, levels, ref=ref, shift_range=min(5, (1 << levels) - 1))
     check_stack(mtb_lib, oracle_mod, imgs, levels, 4, ref)
 
 
 @pytest.mark.parametrize("tol", [0, 1, 4, 17, 255])
-def test_noise_tolerance(mtb_lib, oracle_mod, tol):
+def test_noise_tolerance(search_kernel, mtb_lib, oracle_mod, tol):
     imgs = _natural(7, 301, 211, 3, 5, ref=1)
     check_stack(mtb_lib, oracle_mod, imgs, 5, tol, 1)
 
 
 @pytest.mark.parametrize("kind", ["zeros", "full", "constant", "uniform", "two-level", "stripes"])
-def test_degenerate_content(mtb_lib, oracle_mod, kind):
+def test_degenerate_content(search_kernel, mtb_lib, oracle_mod, kind):
     n, h, w, levels = 3, 130, 290, 5
     g = torch.Generator().manual_seed(5)
     if kind == "zeros":
@@ -81,12 +81,12 @@ def test_degenerate_content(mtb_lib, oracle_mod, kind):
         assert not want["shifts"].any()
 
 
-def test_many_exposures(mtb_lib, oracle_mod):
+def test_many_exposures(search_kernel, mtb_lib, oracle_mod):
     imgs = _natural(11, 200, 150, 9, 4, ref=4)
     check_stack(mtb_lib, oracle_mod, imgs, 4, 4, 4)
 
 
-def test_widest_row(mtb_lib, oracle_mod):
+def test_widest_row(search_kernel, mtb_lib, oracle_mod):
     w, h = 65535, 3
     g = torch.Generator().manual_seed(3)
     imgs = torch.randint(0, 256, (2, h, w, 3), generator=g, dtype=torch.uint8).cuda()
@@ -94,7 +94,7 @@ def test_widest_row(mtb_lib, oracle_mod):
 
 
 @pytest.mark.parametrize("spec", synth.PLAIN_CONFIGS, ids=lambda s: s.name)
-def test_config_parity(mtb_lib, oracle_mod, spec):
+def test_config_parity(search_kernel, mtb_lib, oracle_mod, spec):
     imgs = synth.make_stack(spec, "cuda")
     want = check_stack(mtb_lib, oracle_mod, imgs, spec.levels, spec.noise_tol, spec.ref,
                        maps=spec.w * spec.h <= 12_000_000)
@@ -104,7 +104,7 @@ def test_config_parity(mtb_lib, oracle_mod, spec):
         assert all(ok), (want["shifts"].tolist(), exp.tolist())
 
 
-def test_one_call_matches_stages(mtb_lib, oracle_mod):
+def test_one_call_matches_stages(search_kernel, mtb_lib, oracle_mod):
     spec = synth.small_spec(21, 640, 480, n=4, levels=6, shift_range=30, ref=2)
     imgs = synth.make_stack(spec, "cuda")
     shifts, errs, lsh = mtb_lib.align_stack(imgs, spec.levels, 4, spec.ref, level_outputs=True)
@@ -144,7 +144,7 @@ def test_invalid_arguments_enqueue_nothing(mtb_lib):
         mtb_lib.align_stack(raw, 2, 4, 0)  # base not 16-byte aligned
 
 
-def test_bounded_wait_reports_timeout(mtb_lib):
+def test_bounded_wait_reports_timeout(search_kernel, mtb_lib):
     """A search whose coarse work for pair 0 never reports completion: the work
     that depends on it must give up after the timeout and leave MTB_ERR_TIMEOUT
     in the status word (no hang), and a normal search afterwards is correct."""
@@ -205,7 +205,7 @@ def test_binding_rejects_outputs_it_could_overrun(mtb_lib):
 
 
 @pytest.mark.parametrize("w,h,n,levels,ref", [(64, 48, 3, 4, 1), (640, 480, 4, 6, 2), (2000, 1500, 3, 7, 1)])
-def test_dirty_workspace_one_call(mtb_lib, oracle_mod, w, h, n, levels, ref):
+def test_dirty_workspace_one_call(search_kernel, mtb_lib, oracle_mod, w, h, n, levels, ref):
     """The one-call path on a workspace whose bookkeeping a previous user left
     full of large values (queue head, completion counters, status word, error
     sums): the call's own clearing must come before the search reads any of
