@@ -3,9 +3,11 @@
 
 A step is one pass of the whole path over one exposure stack: one
 mtb_align_stack_ex call, which enqueues the pyramid pass (k_clear, k_pyramid),
-the bitmap pass (k_bitmaps) and the coarse-to-fine shift search (k_search,
-which starts while the bitmaps are still being packed), chained by
-programmatic dependent launch.  The
+the bitmap pass (k_bitmaps) and the coarse-to-fine shift search (the item
+kernel k_search_items, which starts while the bitmaps are still being packed),
+chained by programmatic dependent launch.  The stage split times the search
+on its own, where the library picks the staged kernel (k_search_staged) for
+large stacks.  The
 default workload is the 6000x4000 stack of 7 exposures (6 pairs, 8 levels), the
 largest plain stack.  The metric is aligned MPix/s: full-resolution pixels of
 every aligned pair divided by the step time.  The K timed steps run back to
@@ -73,6 +75,7 @@ LAT_STEPS = 100
 LAT_WARMUP = 10
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
+L2_BYTES = 126 * 1024 * 1024  # GB300 L2 capacity
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
 # ncu capture, keyed by kernel and workload, with the SHA-256 of that kernel's
@@ -93,7 +96,7 @@ def parse_args(argv=None):
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=("gb300", "reference"), default="gb300")
     p.add_argument("--workload", default="stack6000x4000x7")
-    p.add_argument("--min-timed-s", type=float, default=0.5,
+    p.add_argument("--min-timed-s", type=float, default=5.0,
                    help="repeat the K-step timed region until the regions add up to this many seconds")
     p.add_argument("--batch-count", type=int, default=256,
                    help="stacks of the batched-vs-plain record in the default line (0: leave it out)")
@@ -155,6 +158,17 @@ def workload(name: str):
     raise SystemExit(f"unknown workload {name}; choose from {[s.name for s in synth.PLAIN_CONFIGS]}")
 
 
+def plain_config(spec, world: int, buffers: int) -> dict:
+    """The `config` of a plain-stack line, the same for the GPU arm and the
+    reference arm (which aligns the same stack on the host cores)."""
+    return {"workload": spec.name, "w": spec.w, "h": spec.h, "n_exposures": spec.n, "pairs": spec.pairs,
+            "levels": spec.levels, "noise_tol": spec.noise_tol, "ref": spec.ref,
+            "stacks_per_step_per_gpu": 1, "parallelism": f"replicas x{world}",
+            "l2": f"inputs+workspaces rotate over {buffers} device copies"
+                  + (" (the inputs alone > 3x L2)" if buffers * spec.input_bytes > 3 * L2_BYTES
+                     else " (they fit in L2: steps may hit it)")}
+
+
 def algorithmic_bytes(spec) -> dict:
     """Bytes each stage must move for one stack (per step), by the path's design:
     pyramid: read RGB (3 B/px) + write gray of levels 0..min(L-1, 5);
@@ -177,10 +191,13 @@ def kernels_per_step(spec) -> int:
 KERNEL_SOURCES = {  # the files each recorded kernel is built from
     "k_pyramid": ("mtb_pyramid.cu", "mtb_pyramid_dev.cuh", "mtb_device.cuh", "mtb_internal.cuh"),
     "k_bitmaps": ("mtb_bitmaps.cu", "mtb_bitmaps_dev.cuh", "mtb_device.cuh", "mtb_internal.cuh"),
-    "k_search": ("mtb_search.cu", "mtb_search_dev.cuh", "mtb_device.cuh", "mtb_internal.cuh"),
+    "k_search_staged": ("mtb_search.cu", "mtb_search_staged.cuh", "mtb_search_dev.cuh", "mtb_device.cuh",
+                        "mtb_internal.cuh"),
+    "k_search_items": ("mtb_search.cu", "mtb_search_dev.cuh", "mtb_device.cuh", "mtb_internal.cuh"),
     "k_apply_shifts": ("mtb_apply.cu", "mtb_internal.cuh"),
 }
-STAGE_KERNEL = {"pyramid": "k_pyramid", "bitmaps": "k_bitmaps", "search": "k_search"}
+# the search stage runs one of two kernels (mtb_search_kernel tells which)
+STAGE_KERNEL = {"pyramid": "k_pyramid", "bitmaps": "k_bitmaps", "search": "k_search_staged"}
 
 
 def kernel_sources_digest(kernel: str) -> str:
@@ -593,17 +610,19 @@ def run_gb300(args):
     top = max(stage_ms, key=stage_ms.get)
     achieved = abytes[top] / (stage_ms[top] / 1e3) / 1e9
     call = {"pyramid": "mtb_build_pyramids", "bitmaps": "mtb_build_bitmaps", "search": "mtb_search_shifts"}
-    roofline = {"bound": "hbm", "kernel": STAGE_KERNEL[top], "achieved": round(achieved, 1), "peak": peak,
+    kern = dict(STAGE_KERNEL)
+    kern["search"] = "k_search_" + mtb.search_kernel(n, w, h, L, spec.ref, chained=False)
+    roofline = {"bound": "hbm", "kernel": kern[top], "achieved": round(achieved, 1), "peak": peak,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                "traffic": traffic_for(STAGE_KERNEL[top], spec.name), "algorithmic_bytes_per_launch": abytes[top],
+                "traffic": traffic_for(kern[top], spec.name), "algorithmic_bytes_per_launch": abytes[top],
                 "ms_per_launch": round(stage_ms[top], 5),
                 "share_of_staged_step": round(stage_ms[top] / staged_total, 3),
                 "duration_source": f"CUDA events around {call[top]}, {len(sev)} staged steps after the "
                                    f"timed region, same buffers and stream"}
-    stages = {k: {"kernel": STAGE_KERNEL[k], "ms": round(v, 5), "share": round(v / staged_total, 3),
+    stages = {k: {"kernel": kern[k], "ms": round(v, 5), "share": round(v / staged_total, 3),
                   "alg_GBps": round(abytes[k] / (v / 1e3) / 1e9, 1),
                   "frac_of_peak": round(abytes[k] / (v / 1e3) / 1e9 / peak, 4),
-                  "traffic": traffic_for(STAGE_KERNEL[k], spec.name)} for k, v in stage_ms.items()}
+                  "traffic": traffic_for(kern[k], spec.name)} for k, v in stage_ms.items()}
 
     # ---- end to end through the host-buffer entry point ----
     e2e = None
@@ -656,11 +675,8 @@ def run_gb300(args):
             "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-            "config": {"workload": spec.name, "w": w, "h": h, "n_exposures": n, "pairs": spec.pairs,
-                       "levels": L, "noise_tol": spec.noise_tol, "ref": spec.ref,
-                       "stacks_per_step_per_gpu": 1, "parallelism": f"replicas x{world}",
-                       "l2": f"inputs+workspaces rotate over {B} device copies "
-                             f"({B * (spec.input_bytes + wss[0].numel()) / 1e6:.0f} MB > L2)"},
+            "config": plain_config(spec, world, B),
+            "l2_bytes_rotated": B * (spec.input_bytes + wss[0].numel()),
             "latency_ms": {"p50": round(_pct(step_ms, 0.50), 5), "p99": round(_pct(step_ms, 0.99), 5),
                            "runs": len(step_ms), "warmup": LAT_WARMUP},
             "hbm_gbs": round(step_bytes / (ms_per_step / 1e3) / 1e9, 1),
@@ -727,8 +743,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": spec.name, "w": spec.w, "h": spec.h, "n_exposures": spec.n, "pairs": spec.pairs,
-                   "levels": spec.levels, "noise_tol": spec.noise_tol, "ref": spec.ref},
+        "config": plain_config(spec, args.gpus, max(1, args.buffers)),
         "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
                          "host": host_cpu()},
         "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -894,13 +909,17 @@ def run_serve(args):
             th = threading.Thread(target=submitter)
             th.start()
             lat, queue, done_at = [], [], []
+            phases = {"enqueue": [], "device": [], "callback": []}
             same = orc_same = 0
             for i in range(count):
                 while ids[i] is None:
                     time.sleep(0.0002)
                 if isinstance(ids[i], Exception):
                     raise ids[i]
-                shifts, l_ms, q_ms = srv.wait(ids[i])
+                shifts, ph = srv.wait_phases(ids[i])
+                l_ms, q_ms = ph["total"], ph["queue"]
+                for k in phases:
+                    phases[k].append(ph[k])
                 l_ms += slip[i] * 1e3  # from the scheduled arrival
                 lat.append(l_ms)
                 queue.append(q_ms + slip[i] * 1e3)
@@ -918,6 +937,10 @@ def run_serve(args):
                 "p50_ms": round(_pct(lat, 0.50), 3), "p99_ms": round(_pct(lat, 0.99), 3),
                 "queue_p50_ms": round(_pct(queue, 0.50), 3), "queue_p99_ms": round(_pct(queue, 0.99), 3),
                 "submit_slip_p99_ms": round(_pct(slip, 0.99) * 1e3, 3),
+                # where the latency goes (host clock): enqueueing the job's work,
+                # the copy in + alignment + copy out + callback dispatch, the callback
+                "phases_p50_p99_ms": {k: [round(_pct(v, 0.50), 3), round(_pct(v, 0.99), 3)]
+                                      for k, v in phases.items()},
                 "same_as_alone": f"{same}/{count}",
                 "oracle_equal": f"{orc_same}/{count}" if orc is not None else None,
             })

@@ -190,6 +190,17 @@ int mtb_get_last_status(void *stream);
 int mtb_workspace_status(const void *workspace, size_t workspace_bytes, int n_exposures, int w, int h, int levels,
                          void *stream);
 
+/* Which of the library's two search kernels a search of this stack runs on the
+ * calling thread's current device: 1 the staged kernel (bit planes staged in
+ * shared memory, deep levels on thread-block clusters), 0 the item kernel
+ * (persistent work queue).  chained != 0: the search of a whole-stack call
+ * (mtb_align_stack*), which starts while the bitmaps are still being packed;
+ * 0: mtb_search_shifts on its own.  Both compute the same result (Sec. III-A,
+ * III-B); the paper has one search, so this query has no counterpart in it.
+ * Returns MTB_ERR_INVALID_ARG for an invalid stack, MTB_ERR_CUDA if the device
+ * cannot be queried.  Host only; enqueues nothing. */
+int mtb_search_kernel(int n_exposures, int w, int h, int levels, int ref_idx, int chained);
+
 /* Test hook with no counterpart in the paper: runs the search of stage 3 with
  * pair 0's coarse-level work withholding its completion signal, so the work that
  * depends on it waits until timeout_ns (1 ns .. 1 s) runs out.  Returns the
@@ -417,6 +428,15 @@ int mtb_server_poll(mtb_server_t *server, uint64_t job_id);
  * shifts being in host_shifts_out, and the part of it spent waiting for
  * admission. */
 int mtb_server_wait(mtb_server_t *server, uint64_t job_id, double *times_ms);
+
+/* As mtb_server_wait, with the latency split into its phases (host clock,
+ * milliseconds): times_ms (NULL or double[5]) receives [0] submission to the
+ * shifts being in host_shifts_out, [1] waiting for admission, [2] enqueueing
+ * the job's copies and kernels, [3] from then to the completion callback
+ * (the copy in, the alignment, the copy out and the callback's dispatch), [4]
+ * the callback itself.  No counterpart in the paper (serving is this
+ * library's addition). */
+int mtb_server_wait_phases(mtb_server_t *server, uint64_t job_id, double *times_ms);
 
 /* Holds (paused != 0) or resumes admission; queued jobs stay queued. */
 int mtb_server_pause(mtb_server_t *server, int paused);

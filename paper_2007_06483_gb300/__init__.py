@@ -119,6 +119,8 @@ def lib():
             "mtb_align_stack_host": (I, [P, I, I, I, I, I, I, P, P, S, P]),
             "mtb_workspace_status": (I, [P, S, I, I, I, I, P]),
             "mtb_debug_search_withheld": (I, [I, I, I, I, I, P, S, ctypes.c_longlong, P]),
+            "mtb_search_kernel": (I, [I, I, I, I, I, I]),
+            "mtb_server_wait_phases": (I, [P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]),
             "mtb_batch_workspace_bytes": (S, [P, I]),
             "mtb_batch_create": (I, [P, I, P, S, ctypes.POINTER(ctypes.c_void_p)]),
             "mtb_batch_run": (I, [P, P]),
@@ -339,6 +341,15 @@ def workspace_status(workspace, n: int, w: int, h: int, levels: int, stream=None
     """Status word of the last search in `workspace` (MTB_OK or MTB_ERR_TIMEOUT)."""
     ws_ptr, ws_bytes = _stage_workspace(workspace)
     return int(lib().mtb_workspace_status(ws_ptr, ws_bytes, n, w, h, levels, _stream(stream)))
+
+
+def search_kernel(n: int, w: int, h: int, levels: int, ref_idx: int = 0, chained: bool = False) -> str:
+    """mtb_search_kernel: "staged" or "items", the search kernel a search of this
+    stack runs on the current device (chained: inside a whole-stack call)."""
+    rc = int(lib().mtb_search_kernel(n, w, h, levels, ref_idx, 1 if chained else 0))
+    if rc < 0:
+        raise MtbError(rc, "mtb_search_kernel")
+    return "staged" if rc == 1 else "items"
 
 
 def get_last_status(stream=None) -> int:
@@ -595,6 +606,17 @@ class Server:
         _, out = self._jobs.pop(job_id, (None, None))
         _check(rc, "mtb_server_wait")
         return out, t[0], t[1]
+
+    def wait_phases(self, job_id: int):
+        """Blocks until the job completes; returns (shifts, phases) with phases
+        the latency split of mtb_server_wait_phases, in ms: total, queue,
+        enqueue, device (copy in, alignment, copy out, callback dispatch),
+        callback.  Raises MtbError if the job failed."""
+        t = (ctypes.c_double * 5)()
+        rc = lib().mtb_server_wait_phases(self._h, job_id, t)
+        _, out = self._jobs.pop(job_id, (None, None))
+        _check(rc, "mtb_server_wait_phases")
+        return out, dict(zip(("total", "queue", "enqueue", "device", "callback"), list(t)))
 
     def pause(self, paused: bool = True):
         _check(lib().mtb_server_pause(self._h, int(bool(paused))), "mtb_server_pause")

@@ -410,6 +410,15 @@ int mtb_workspace_status(const void *workspace, size_t workspace_bytes, int n_ex
     return status;
 }
 
+int mtb_search_kernel(int n_exposures, int w, int h, int levels, int ref_idx, int chained) {
+    const int rc = check_stack_args(n_exposures, w, h, levels, 0, ref_idx);
+    if (rc != MTB_OK) return rc;
+    mtb_layout_t L;
+    compute_layout(n_exposures, w, h, levels, &L);
+    const int k = search_kernel_choice(L, ref_idx, chained != 0);
+    return k < 0 ? MTB_ERR_CUDA : k;
+}
+
 int mtb_debug_search_withheld(int n_exposures, int w, int h, int levels, int ref_idx, void *workspace,
                               size_t workspace_bytes, long long timeout_ns, void *stream) {
     mtb_layout_t L;

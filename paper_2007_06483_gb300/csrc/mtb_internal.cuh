@@ -141,6 +141,10 @@ cudaError_t launch_search_ex(const mtb_layout_t &L, int ref_idx, uint8_t *ws, in
                              unsigned long long timeout_ns, int withhold_pair, bool overlap = false,
                              bool chain = false);
 
+// Which kernel a search of this stack runs on the current device: 1 the
+// staged kernel, 0 the item kernel, -1 on a CUDA error.
+int search_kernel_choice(const mtb_layout_t &L, int ref_idx, bool overlap);
+
 int device_sm_count();
 
 // Whole alignment of one stack in one persistent launch (mtb_engine.cu).

@@ -461,6 +461,34 @@ cudaError_t launch_items(const mtb_layout_t &L, int ref_idx, uint8_t *ws, int32_
 
 }  // namespace
 
+namespace {
+
+// Whether a search of this stack runs the staged kernel (else the item kernel).
+// The staged kernel needs whole SMs (one CTA each) in clusters: right behind
+// the bitmap pass it starts only once bitmap CTAs have left whole SMs, and the
+// item kernel, whose CTAs fit beside them, overlaps that pass better.  On its
+// own it wins from about 64 M pair-pixels at level 0 (6000x4000x7: 62.0
+// against 69.6 us; 4000x3000x3: 41.7 against 40.7 us).  MTB_SEARCH_ITEMS=1
+// (0) forces the item (staged) kernel, for comparisons and tests.
+bool wants_staged(const mtb_layout_t &L, bool overlap) {
+    const long long pair_pixels = (long long)L.w * L.h * (L.n - 1);
+    const int forced = env_int("MTB_SEARCH_ITEMS", -1);
+    return forced == 0 || (forced != 1 && !overlap && pair_pixels >= (64ll << 20));
+}
+
+}  // namespace
+
+int search_kernel_choice(const mtb_layout_t &L, int ref_idx, bool overlap) {
+    if (!wants_staged(L, overlap)) return 0;
+    ClusterShape shape;
+    if (cluster_shape(overlap, &shape) != cudaSuccess) return -1;
+    StagedPlan P;
+    return plan_staged_search(L, ref_idx, shape.cluster, shape.clusters, nullptr, nullptr, nullptr, 1, -1, 0,
+                              env_int("MTB_SEARCH_SPLIT", -1), &P) == MTB_OK
+               ? 1
+               : 0;
+}
+
 cudaError_t launch_search_ex(const mtb_layout_t &L, int ref_idx, uint8_t *ws, int32_t *shifts_out,
                              uint32_t *level_errs_out, int32_t *level_shifts_out, cudaStream_t s, bool chained,
                              unsigned long long timeout_ns, int withhold_pair, bool overlap, bool chain) {
@@ -468,18 +496,9 @@ cudaError_t launch_search_ex(const mtb_layout_t &L, int ref_idx, uint8_t *ws, in
     cudaError_t err = cluster_shape(overlap, &shape);
     if (err != cudaSuccess) return err;
     // MTB_SEARCH_SPLIT (the finest level the clusters search) overrides the
-    // planner's choice, for tuning; MTB_SEARCH_ITEMS=1 (0) forces the item
-    // (staged) kernel, for comparisons and tests
-    // The staged kernel needs whole SMs (one CTA each) in clusters: right behind
-    // the bitmap pass it starts only once bitmap CTAs have left whole SMs, and
-    // the item kernel, whose CTAs fit beside them, overlaps that pass better.
-    // On its own it wins from about 64 M pair-pixels at level 0 (6000x4000x7:
-    // 62.0 against 69.6 us; 4000x3000x3: 41.7 against 40.7 us).
-    const long long pair_pixels = (long long)L.w * L.h * (L.n - 1);
-    const int forced = env_int("MTB_SEARCH_ITEMS", -1);
-    const bool staged = forced == 0 || (forced != 1 && !overlap && pair_pixels >= (64ll << 20));
+    // planner's choice, for tuning
     StagedPlan P;
-    if (!staged ||
+    if (!wants_staged(L, overlap) ||
         plan_staged_search(L, ref_idx, shape.cluster, shape.clusters, shifts_out, level_errs_out, level_shifts_out,
                            timeout_ns, withhold_pair, chain ? 1 : 0, env_int("MTB_SEARCH_SPLIT", -1),
                            &P) != MTB_OK)

@@ -50,7 +50,7 @@ struct Job {
     size_t bytes = 0, off = 0;
     int slot = -1;
     int status = kRunning;
-    Clock::time_point t_submit, t_admit, t_done;
+    Clock::time_point t_submit, t_admit, t_enqueued, t_callback, t_done;
 };
 
 struct SlotCtx {
@@ -115,10 +115,12 @@ void finish_locked(mtb_server *s, int slot, int status) {
 
 // Host function at the end of a job's compute stream.  Makes no CUDA call.
 void CUDART_CB job_done(void *p) {
+    const Clock::time_point t_cb = Clock::now();
     SlotCtx *c = static_cast<SlotCtx *>(p);
     mtb_server *s = c->server;
     std::lock_guard<std::mutex> lock(s->mu);
     Job &job = *s->running[c->slot];
+    job.t_callback = t_cb;
     const SlotResult &r = s->results[c->slot];
     std::memcpy(job.desc.host_shifts_out, r.shifts, (size_t)job.desc.n_exposures * 2 * sizeof(int32_t));
     finish_locked(s, c->slot, r.status == 0 ? MTB_OK : r.status);
@@ -190,6 +192,7 @@ void worker_loop(mtb_server *s) {
         s->peak_running = std::max(s->peak_running, s->n_running);
         lock.unlock();
         const int rc = enqueue_job(s, *job);
+        const Clock::time_point t_enq = Clock::now();
         if (rc != MTB_OK) {
             // nothing of this job may still run when its memory is given back
             cudaStreamSynchronize(s->compute[slot]);
@@ -197,6 +200,8 @@ void worker_loop(mtb_server *s) {
             cudaGetLastError();
         }
         lock.lock();
+        job->t_enqueued = t_enq;
+        if (job->t_callback < t_enq) job->t_callback = t_enq;  // (the callback may already have run)
         if (rc != MTB_OK) finish_locked(s, slot, rc);
     }
 }
@@ -327,7 +332,9 @@ int mtb_server_poll(mtb_server_t *s, uint64_t job_id) {
     return it == s->jobs.end() ? MTB_ERR_INVALID_ARG : it->second->status;
 }
 
-int mtb_server_wait(mtb_server_t *s, uint64_t job_id, double *times_ms) {
+namespace {
+
+int wait_job(mtb_server_t *s, uint64_t job_id, double *times_ms, int n_times) {
     if (!s) return MTB_ERR_INVALID_ARG;
     std::unique_lock<std::mutex> lock(s->mu);
     auto it = s->jobs.find(job_id);
@@ -336,11 +343,23 @@ int mtb_server_wait(mtb_server_t *s, uint64_t job_id, double *times_ms) {
     s->cv_done.wait(lock, [&j] { return j->status != kRunning; });
     if (times_ms) {
         using ms = std::chrono::duration<double, std::milli>;
-        times_ms[0] = ms(j->t_done - j->t_submit).count();
-        times_ms[1] = ms(j->t_admit - j->t_submit).count();
+        const bool ran = j->t_enqueued != Clock::time_point{};  // admitted and enqueued
+        const double t[5] = {ms(j->t_done - j->t_submit).count(), ms(j->t_admit - j->t_submit).count(),
+                             ran ? ms(j->t_enqueued - j->t_admit).count() : 0.0,
+                             ran ? ms(j->t_callback - j->t_enqueued).count() : 0.0,
+                             ran ? ms(j->t_done - j->t_callback).count() : 0.0};
+        for (int k = 0; k < n_times && k < 5; ++k) times_ms[k] = t[k];
     }
     s->jobs.erase(job_id);
     return j->status;
+}
+
+}  // namespace
+
+int mtb_server_wait(mtb_server_t *s, uint64_t job_id, double *times_ms) { return wait_job(s, job_id, times_ms, 2); }
+
+int mtb_server_wait_phases(mtb_server_t *s, uint64_t job_id, double *times_ms) {
+    return wait_job(s, job_id, times_ms, 5);
 }
 
 int mtb_server_pause(mtb_server_t *s, int paused) {
