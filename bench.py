@@ -81,11 +81,21 @@ L2_BYTES = 126 * 1024 * 1024  # GB300 L2 capacity
 # ncu capture, keyed by kernel and workload, with the SHA-256 of that kernel's
 # sources at capture time; reported only while those sources are unchanged.
 NCU_TRAFFIC = {
-    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum (cold cache), one
-    # launch each: k_pyramid of the 4000x3000x3 stack (109.70 MB read + 6.95 MB
+    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum (cold cache), per
+    # launch: k_pyramid of the 4000x3000x3 stack (109.70 MB read + 6.95 MB
     # written) and k_apply_shifts of the 6000x4000x7 stack (496.81 + 458.26 MB)
     ("k_pyramid", "stack4000x3000x3"): {"bytes": 116647680, "sources_sha256": "51d50f00dfb4fe6bf0b3fbd829edfbd37d05433985f0057cd6a55eace28f9b84"},
     ("k_apply_shifts", "apply6000x4000x7"): {"bytes": 955071744, "sources_sha256": "e265c02bbfa6e0cda0bd4c35ae4a6118438da478c9b3a3a35471b1d9ce84ba18"},
+    # the 6000x4000x7 stack, `bench.py --profile --steps 2 --warmup 2` under
+    # ncu, mean over the captured launches: k_pyramid 536.91 MB read + 167.51 MB
+    # written (3 launches), k_bitmaps 224.69 + 6.22 MB (3), k_search_staged
+    # 56.38 + 0.00 MB (2), k_search_items 56.33 + 0.00 MB (2). Written bytes
+    # still dirty in L2 when a launch ends are not counted, hence writes below
+    # the algorithmic figure
+    ("k_pyramid", "stack6000x4000x7"): {"bytes": 704418389, "sources_sha256": "90df573d5d3294bac4d769b0160e4d7e766b85a244e1446049608932cab768bb"},
+    ("k_bitmaps", "stack6000x4000x7"): {"bytes": 230917461, "sources_sha256": "bb35a732ebbd013dbd2dcc3ec1c9480b52044fe74147e42a75467b612fb6862c"},
+    ("k_search_staged", "stack6000x4000x7"): {"bytes": 56375680, "sources_sha256": "716614be7b5266bc8dbed05da8e7af8e32025b752d9e61a500b693b8fc8857d7"},
+    ("k_search_items", "stack6000x4000x7"): {"bytes": 56334080, "sources_sha256": "d2020c4d98cdd95aec14546405557de8c1b8e067c3ed568c2f228764cd2c7a21"},
 }
 
 
@@ -104,6 +114,9 @@ def parse_args(argv=None):
                    help="only run this many plain steps of the workload (for ncu captures) and exit")
     p.add_argument("--buffers", type=int, default=4, help="device copies rotated over the steps")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--profile", action="store_true",
+                   help="only the kernels, for ncu: W one-call steps, then K one-call steps and K stage-split steps "
+                        "of the plain workload; prints one line of shifts")
     p.add_argument("--cpu-threads", type=int, default=0,
                    help="threads of the threaded oracle baseline (0: the usable cores; 1: skip it)")
     p.add_argument("--no-e2e", action="store_true")
@@ -815,6 +828,28 @@ def h2d_link_gbs(host, dev, stream, reps: int = 5) -> float:
     return host.numel() / (best / 1e3) / 1e9
 
 
+def h2d_copy_probe(pool, dev, stream, count: int = 40, gap_s: float = 0.02) -> dict:
+    """Single 504 MB pinned host-to-device copies, one at a time and `gap_s`
+    apart (a low offered load), each timed with CUDA events: how the copy a
+    served job starts with varies by itself, with no alignment and no server
+    around it."""
+    import torch
+
+    d = torch.empty(pool[0].shape, dtype=pool[0].dtype, device=dev)
+    ms = []
+    for k in range(count):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        d.copy_(pool[k % len(pool)], non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms.append(e0.elapsed_time(e1))
+        time.sleep(gap_s)
+    del d
+    return {"copies": count, "gap_ms": gap_s * 1e3, "p50_ms": round(_pct(ms, 0.50), 3),
+            "p99_ms": round(_pct(ms, 0.99), 3), "max_ms": round(max(ms), 3)}
+
+
 def run_serve(args):
     """Poisson arrivals of 6000x4000x7 jobs (synth.serve_specs, pinned host
     memory) into the serving loop under a device-memory budget, swept over the
@@ -869,6 +904,7 @@ def run_serve(args):
     del resident, ws, outp
     torch.cuda.empty_cache()
     link_gbs = h2d_link_gbs(pool[0], dev, stream)
+    copy_probe = h2d_copy_probe(pool, dev, stream)
     sp0 = specs[0]
     px = sp0.aligned_pixels
     job_bytes = mtb.job_bytes(sp0.n, sp0.w, sp0.h, sp0.levels, sp0.noise_tol, sp0.ref)
@@ -966,6 +1002,9 @@ def run_serve(args):
                      "peak_kind": "measured in this run: best of 5 pinned 504 MB host->device copies",
                      "unit": "GB/s", "frac": round(best["h2d_gbs"] / link_gbs, 4), "traffic": None},
         "server_stats": st,
+        # the device phase's tail comes from the copy in: the same copies
+        # alone, spaced like a low offered load
+        "h2d_copy_alone": copy_probe,
         "results_same_alone_and_in_mix": bool(all_same),
         "alone_equal_oracle": (f"{sum(torch.equal(a, o) for a, o in zip(alone, orc))}/{len(alone)}"
                                if orc is not None else None),
@@ -1117,9 +1156,42 @@ def run_paper(args):
     print(json.dumps(line), flush=True)
 
 
+def run_profile(args):
+    """The plain workload's kernels and nothing else, as the target of ncu
+    captures: W one-call steps (k_clear, k_pyramid, k_bitmaps, k_search_items),
+    then K one-call steps, then K stage-split steps (k_pyramid, k_bitmaps,
+    k_clear_search + the search kernel the library picks for the stage)."""
+    import torch
+
+    from paper_2007_06483_gb300 import build as cuda_build
+
+    cuda_build.build()
+    import paper_2007_06483_gb300 as mtb
+    from paper_2007_06483_gb300 import synth
+
+    spec = workload(args.workload)
+    n, w, h, L = spec.n, spec.w, spec.h, spec.levels
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream(dev)
+    images = synth.make_stack(spec, dev)
+    ws = mtb.new_workspace(n, w, h, L, device=dev)
+    out = torch.empty((n, 2), dtype=torch.int32, device=dev)
+    for _ in range(args.warmup + args.steps):
+        mtb.align_stack(images, L, spec.noise_tol, spec.ref, workspace=ws, out=out, stream=stream)
+    for _ in range(args.steps):
+        mtb.build_pyramids(images, L, ws, stream)
+        mtb.build_bitmaps(n, w, h, L, spec.noise_tol, ws, stream)
+        mtb.search_shifts(n, w, h, L, spec.ref, ws, out, None, None, stream)
+    torch.cuda.synchronize(dev)
+    print(json.dumps({"profile": spec.name, "search_kernel": mtb.search_kernel(n, w, h, L, spec.ref),
+                      "shifts": out.cpu().tolist()}), flush=True)
+
+
 def main(argv=None):
     args = parse_args(argv)
-    if args.impl == "reference":
+    if args.profile:
+        run_profile(args)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.workload.startswith("batch"):
         run_batch(args)
