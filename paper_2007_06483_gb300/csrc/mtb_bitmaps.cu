@@ -16,9 +16,11 @@
 // the MSB of every byte of
 //     ge(x) = (x & ~T) | ((x ^ ~T) & ((x | 0x80..) - (T & 0x7f..)))
 // is [x_byte >= t]  (T = t in every byte; the subtraction cannot borrow across
-// bytes because each byte of the minuend is >= 0x80).  The 4 MSBs of a word are
-// gathered into 4 adjacent bits by one multiply: bits 7, 15, 23, 31 times
-// 2^21 + 2^14 + 2^7 + 1 land on bits 28..31 without carries.
+// bytes because each byte of the minuend is >= 0x80).  The MSBs of two words
+// are merged into one (the first's shifted down by 4) and gathered into 8
+// adjacent bits by one multiply: bits 3, 7, 11, ..., 31 times 2^21 + 2^14 +
+// 2^7 + 1 land on bits 24..31 without carries; byte permutes then place the
+// four top bytes.
 // The exclusion test is that comparison on the per-byte absolute difference
 // |g - m| (__vabsdiffu4, a single SIMD instruction): eb = [|g - m| >= tol + 1].
 #include "mtb_bitmaps_dev.cuh"

@@ -27,39 +27,42 @@ struct ByteGE {
 // The thresholds of one (exposure, level): tb = [g >= m + 1] and, since
 // g < m - tol or g > m + tol is |g - m| > tol, eb = [|g - m| >= tol + 1] on the
 // per-byte absolute difference (one SIMD instruction); a test that can never
-// hold (m = 255, tol = 255) is masked out instead.
+// hold (m = 255, tol = 255) clears its whole output word instead.
 struct Thresholds {
     uint32_t m4;  // the median in every byte
     ByteGE tb, eb;
-    uint32_t tb_mask, eb_mask;
+    uint32_t tb_all, eb_all;
     __device__ __forceinline__ Thresholds(int m, int tol)
         : m4((uint32_t)m * 0x01010101u), tb((uint32_t)min(m + 1, 255)), eb((uint32_t)min(tol + 1, 255)),
-          tb_mask(m < 255 ? kHi : 0u), eb_mask(tol < 255 ? kHi : 0u) {}
+          tb_all(m < 255 ? 0xffffffffu : 0u), eb_all(tol < 255 ? 0xffffffffu : 0u) {}
 };
 
-// MSBs of bytes 0..3 of x (already masked to kHi) -> bits 0..3.
-__device__ __forceinline__ uint32_t msb_nibble_top(uint32_t x) { return x * 0x00204081u; }
+// The flags (byte MSBs) of two gray words k and k + 1 -> one product whose top
+// byte holds the 8 flags in pixel order: word k's MSBs moved to bits 3, 11,
+// 19, 27 and word k + 1's at 7, 15, 23, 31, times 2^21 + 2^14 + 2^7 + 1, put
+// bit 8j + 3 on 24 + j and bit 8j + 7 on 28 + j; every other partial product
+// lands on a distinct bit below 24 or past 31, so nothing carries into the top
+// byte.
+__device__ __forceinline__ uint32_t gather_pair(uint32_t r0, uint32_t r1) {
+    return ((((r0 & kHi) >> 4) | (r1 & kHi)) * 0x00204081u);
+}
+// The top bytes of four such products, in order, as one word.
+__device__ __forceinline__ uint32_t top_bytes(uint32_t p0, uint32_t p1, uint32_t p2, uint32_t p3) {
+    return __byte_perm(__byte_perm(p0, p1, 0x0073u), __byte_perm(p2, p3, 0x0073u), 0x5410u);
+}
 
 // tb and eb words of 32 gray pixels in 8 little-endian words; only the first
 // nvalid pixels can be set.
 __device__ __forceinline__ uint2 pack_bits(const uint32_t (&v)[8], const Thresholds &th, int nvalid) {
-    uint32_t tb = 0, eb = 0;
+    uint32_t pt[4], pe[4];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        const uint32_t tm = th.tb(v[k]) & th.tb_mask;
-        const uint32_t em = th.eb(__vabsdiffu4(v[k], th.m4)) & th.eb_mask;
-        // top nibble of the product holds the 4 flags; move it to bits 4k..4k+3
-        const uint32_t pt = msb_nibble_top(tm), pe = msb_nibble_top(em);
-        if (k == 7) {
-            tb |= pt & 0xf0000000u;
-            eb |= pe & 0xf0000000u;
-        } else {
-            tb |= (pt >> (28 - 4 * k)) & (0xfu << (4 * k));
-            eb |= (pe >> (28 - 4 * k)) & (0xfu << (4 * k));
-        }
+    for (int k = 0; k < 8; k += 2) {
+        pt[k / 2] = gather_pair(th.tb(v[k]), th.tb(v[k + 1]));
+        pe[k / 2] = gather_pair(th.eb(__vabsdiffu4(v[k], th.m4)), th.eb(__vabsdiffu4(v[k + 1], th.m4)));
     }
     const uint32_t keep = nvalid >= 32 ? 0xffffffffu : ((1u << nvalid) - 1u);
-    return make_uint2(tb & keep, eb & keep);
+    return make_uint2(top_bytes(pt[0], pt[1], pt[2], pt[3]) & keep & th.tb_all,
+                      top_bytes(pe[0], pe[1], pe[2], pe[3]) & keep & th.eb_all);
 }
 
 // Levels tile_levels..levels-1 of exposure e, built by one CTA.  Each level
