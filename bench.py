@@ -829,25 +829,45 @@ def h2d_link_gbs(host, dev, stream, reps: int = 5) -> float:
 
 
 def h2d_copy_probe(pool, dev, stream, count: int = 40, gap_s: float = 0.02) -> dict:
-    """Single 504 MB pinned host-to-device copies, one at a time and `gap_s`
-    apart (a low offered load), each timed with CUDA events: how the copy a
-    served job starts with varies by itself, with no alignment and no server
-    around it."""
+    """Single 504 MB pinned host-to-device transfers, one at a time and `gap_s`
+    apart (a low offered load), each timed with CUDA events, with no alignment
+    and no server around them: by a copy engine (cudaMemcpyAsync) and by SM
+    loads (a PyTorch elementwise kernel reading the pinned buffer through
+    unified addressing, as the server's copy kernel does).  A copy engine idle
+    for milliseconds is slow to start its next copy; SM loads are not."""
     import torch
 
+    class _Cai:  # the pinned buffer as a device array at the same address
+        def __init__(self, t):
+            self.__cuda_array_interface__ = {"shape": (t.numel() // 8,), "typestr": "<i8",
+                                             "data": (t.data_ptr(), False), "version": 3}
+
     d = torch.empty(pool[0].shape, dtype=pool[0].dtype, device=dev)
-    ms = []
-    for k in range(count):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        d.copy_(pool[k % len(pool)], non_blocking=True)
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        ms.append(e0.elapsed_time(e1))
-        time.sleep(gap_s)
+    d64 = d.view(-1).view(torch.int64)
+    views = [torch.as_tensor(_Cai(p), device=dev) if p.is_pinned() and p.numel() % 8 == 0 else None for p in pool]
+    out = {}
+    for mode in ("copy_engine", "sm_loads"):
+        ms = []
+        for k in range(count):
+            src = pool[k % len(pool)]
+            v = views[k % len(pool)]
+            if mode == "sm_loads" and v is None:
+                continue
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            if mode == "copy_engine":
+                d.copy_(src, non_blocking=True)
+            else:
+                torch.bitwise_or(v, 0, out=d64)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms.append(e0.elapsed_time(e1))
+            time.sleep(gap_s)
+        if ms:
+            out[mode] = {"copies": len(ms), "gap_ms": gap_s * 1e3, "p50_ms": round(_pct(ms, 0.50), 3),
+                         "p99_ms": round(_pct(ms, 0.99), 3), "max_ms": round(max(ms), 3)}
     del d
-    return {"copies": count, "gap_ms": gap_s * 1e3, "p50_ms": round(_pct(ms, 0.50), 3),
-            "p99_ms": round(_pct(ms, 0.99), 3), "max_ms": round(max(ms), 3)}
+    return out
 
 
 def run_serve(args):
@@ -997,7 +1017,7 @@ def run_serve(args):
                                         "ms_per_job": round(plain_ms / len(specs), 4)},
         "e2e": {"value": best["mpix_s"], "unit": UNIT, "h2d_bytes_per_step": int(sp0.input_bytes),
                 "d2h_bytes_per_step": int(sp0.n * 8)},
-        "roofline": {"bound": "h2d_link", "kernel": "cudaMemcpyAsync host->device (copy engines)",
+        "roofline": {"bound": "h2d_link", "kernel": "k_copy_in (SM loads of pinned host memory over NVLink-C2C)",
                      "achieved": best["h2d_gbs"], "peak": round(link_gbs, 1),
                      "peak_kind": "measured in this run: best of 5 pinned 504 MB host->device copies",
                      "unit": "GB/s", "frac": round(best["h2d_gbs"] / link_gbs, 4), "traffic": None},

@@ -394,8 +394,10 @@ typedef struct mtb_server_config {
 } mtb_server_config_t;
 
 typedef struct mtb_job {
-    const uint8_t *host_images;  /* host [n][h][w][3] uint8, valid until the job completes;
-                                    pinned memory lets the copy overlap other work */
+    const uint8_t *host_images;  /* host [n][h][w][3] uint8, valid until the job completes.
+                                    Page-locked (pinned) memory, 16-byte aligned, is read
+                                    by a copy kernel over the host link; other memory is
+                                    copied by cudaMemcpyAsync */
     int n_exposures, w, h, levels, noise_tol, ref_idx;  /* as for mtb_align_stack */
     int32_t *host_shifts_out;    /* host int32 [n][2], written when the job completes */
 } mtb_job_t;

@@ -32,6 +32,60 @@ int device_sm_count() {
     return g_sm_count[dev];
 }
 
+namespace {
+
+constexpr int kCopyCtas = 32, kCopyThreads = 256, kCopyUnroll = 8;  // eight 16-byte loads in flight a thread
+
+__global__ void __launch_bounds__(kCopyThreads) k_copy_in(const uint4 *__restrict__ src, uint4 *__restrict__ dst,
+                                                          size_t n) {
+    const size_t n16 = n / 16, stride = (size_t)gridDim.x * blockDim.x;
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + (kCopyUnroll - 1) * stride < n16; i += kCopyUnroll * stride) {
+        uint4 v[kCopyUnroll];
+#pragma unroll
+        for (int k = 0; k < kCopyUnroll; ++k) v[k] = __ldcs(src + i + k * stride);
+#pragma unroll
+        for (int k = 0; k < kCopyUnroll; ++k) dst[i + k * stride] = v[k];
+    }
+    for (; i < n16; i += stride) dst[i] = __ldcs(src + i);
+    const size_t tail = n - n16 * 16;
+    if (blockIdx.x == 0 && threadIdx.x < tail)
+        reinterpret_cast<uint8_t *>(dst + n16)[threadIdx.x] = reinterpret_cast<const uint8_t *>(src + n16)[threadIdx.x];
+}
+
+__global__ void k_copy_out(const int32_t *__restrict__ src_a, int32_t *dst_a, int na, const int32_t *__restrict__ src_b,
+                           int32_t *dst_b, int nb) {
+    for (int i = threadIdx.x; i < na; i += blockDim.x) dst_a[i] = __ldcg(src_a + i);
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) dst_b[i] = __ldcg(src_b + i);
+    __threadfence_system();
+}
+
+}  // namespace
+
+const uint8_t *host_device_view(const void *p) {
+    cudaPointerAttributes a;
+    if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer || (reinterpret_cast<uintptr_t>(a.devicePointer) & 15))
+        return nullptr;
+    return static_cast<const uint8_t *>(a.devicePointer);
+}
+
+cudaError_t launch_copy_in(const uint8_t *src, uint8_t *dst, size_t n, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    k_copy_in<<<kCopyCtas, kCopyThreads, 0, s>>>(reinterpret_cast<const uint4 *>(src), reinterpret_cast<uint4 *>(dst),
+                                                 n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy_out(const int32_t *src_a, int32_t *dst_a, int na, const int32_t *src_b, int32_t *dst_b,
+                            int nb, cudaStream_t s) {
+    k_copy_out<<<1, 64, 0, s>>>(src_a, dst_a, na, src_b, dst_b, nb);
+    return cudaGetLastError();
+}
+
 int check_stack_args(int n, int w, int h, int levels, int noise_tol, int ref_idx) {
     int rc = check_dims(n, w, h, levels);
     if (rc != MTB_OK) return rc;
@@ -195,15 +249,20 @@ int enqueue_banded(const uint8_t *host_images, uint8_t *d_img, const mtb_layout_
         cudaStreamSynchronize(p->copy);
         return MTB_ERR_CUDA;
     };
+    // page-locked images are read by the copy kernel, the rest (and bands that
+    // start off a 16-byte boundary) by the copy engine
+    const uint8_t *view = host_device_view(host_images);
     int k = 0;
     for (int e = 0; e < L.n; ++e)
         for (int b = 0; b < bands; ++b, ++k) {
             const long long r0 = tile_rows * b / bands, r1 = tile_rows * (b + 1) / bands;
             const size_t y0 = (size_t)r0 * kTileRows, y1 = (size_t)(r1 * kTileRows < L.h ? r1 * kTileRows : L.h);
             const size_t off = ((size_t)e * L.h + y0) * row_bytes, len = (y1 - y0) * row_bytes;
-            if (cudaMemcpyAsync(d_img + off, host_images + off, len, cudaMemcpyHostToDevice, p->copy) != cudaSuccess ||
-                cudaEventRecord(p->band[k], p->copy) != cudaSuccess)
-                return fail();
+            const cudaError_t err = view && (off & 15) == 0
+                                        ? launch_copy_in(view + off, d_img + off, len, p->copy)
+                                        : cudaMemcpyAsync(d_img + off, host_images + off, len, cudaMemcpyHostToDevice,
+                                                          p->copy);
+            if (err != cudaSuccess || cudaEventRecord(p->band[k], p->copy) != cudaSuccess) return fail();
         }
     if (launch_clear_stack(L, ws, s) != cudaSuccess) return fail();
     k = 0;
@@ -467,12 +526,19 @@ int mtb_align_stack_host(const uint8_t *host_images, int n_exposures, int w, int
         if (rc == MTB_OK)
             rc = cuda_status(launch_search(L, ref_idx, ws, d_shifts, nullptr, nullptr, s, true, true, false));
     } else {
-        rc = cuda_status(cudaMemcpyAsync(d_img, host_images, img_bytes, cudaMemcpyHostToDevice, s));
+        const uint8_t *view = host_device_view(host_images);
+        rc = cuda_status(view ? launch_copy_in(view, d_img, img_bytes, s)
+                              : cudaMemcpyAsync(d_img, host_images, img_bytes, cudaMemcpyHostToDevice, s));
         if (rc == MTB_OK) rc = run_all(d_img, L, noise_tol, ref_idx, ws, d_shifts, nullptr, nullptr, s);
     }
-    if (rc == MTB_OK)
-        rc = cuda_status(cudaMemcpyAsync(host_shifts_out, d_shifts, (size_t)n_exposures * 2 * sizeof(int32_t),
-                                         cudaMemcpyDeviceToHost, s));
+    if (rc == MTB_OK) {
+        // page-locked output is written by SM stores, like the input
+        int32_t *out_view = reinterpret_cast<int32_t *>(const_cast<uint8_t *>(host_device_view(host_shifts_out)));
+        rc = cuda_status(out_view ? launch_copy_out(d_shifts, out_view, n_exposures * 2, nullptr, nullptr, 0, s)
+                                  : cudaMemcpyAsync(host_shifts_out, d_shifts,
+                                                    (size_t)n_exposures * 2 * sizeof(int32_t),
+                                                    cudaMemcpyDeviceToHost, s));
+    }
     rc = release(base, owned, s, rc);
     if (cudaStreamSynchronize(s) != cudaSuccess && rc == MTB_OK) rc = MTB_ERR_CUDA;
     return rc;

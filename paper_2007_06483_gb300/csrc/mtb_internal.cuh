@@ -147,6 +147,23 @@ int search_kernel_choice(const mtb_layout_t &L, int ref_idx, bool overlap);
 
 int device_sm_count();
 
+// Host memory moved by SM loads and stores instead of copy engines.  A copy
+// engine that has been idle for some milliseconds is slow to start its next
+// copy (a 504 MB copy: 2.4 ms back to back, p99 19 ms with 20 ms between
+// copies, p90 34 ms with 100 ms); SM loads of the same page-locked memory keep
+// their pace (p99 2.4 and 4.7 ms) at the same ~210 GB/s.
+// The address at which a kernel reaches host buffer p: non-null only for
+// page-locked memory seen through unified addressing, 16-byte aligned.
+const uint8_t *host_device_view(const void *p);
+// dst[0, n) = src[0, n), src from host_device_view, dst device memory, both
+// 16-byte aligned: 32 CTAs, enough to keep the host link busy.
+cudaError_t launch_copy_in(const uint8_t *src, uint8_t *dst, size_t n, cudaStream_t s);
+// dst_a[0, na) = src_a[0, na) and dst_b[0, nb) = src_b[0, nb) (int32 words,
+// src in device memory, dst from host_device_view or null when n is 0), then a
+// system-scope fence: results handed to the host with no copy engine.
+cudaError_t launch_copy_out(const int32_t *src_a, int32_t *dst_a, int na, const int32_t *src_b, int32_t *dst_b,
+                            int nb, cudaStream_t s);
+
 // Whole alignment of one stack in one persistent launch (mtb_engine.cu).
 cudaError_t launch_engine_single(const mtb_layout_t &L, const uint8_t *images, uint8_t *ws, int tol, int ref,
                                  int32_t *shifts_out, uint32_t *level_errs_out, int32_t *level_shifts_out,

@@ -8,7 +8,13 @@
 // while other jobs are on the GPU.  For an admitted job it enqueues
 //   - the copy of its exposures to the device (Sec. III-B copies each exposure
 //     to the GPU once), split over the copy streams, which serve jobs in
-//     admission order so that the first admitted job's copy finishes first;
+//     admission order so that the first admitted job's copy finishes first.
+//     Page-locked host memory is read by a copy kernel straight over the host
+//     link: a copy engine that has been idle for some milliseconds takes up to
+//     ~15x longer for its next 504 MB copy (2.4 ms back to back; p99 19 ms
+//     with 20 ms between copies, p90 34 ms with 100 ms), while SM loads of the
+//     same memory keep their pace (p99 2.4 and 4.7 ms).  Pageable memory goes
+//     through cudaMemcpyAsync;
 //   - on the job's compute stream, after those copies: the whole alignment
 //     (pyramids, bitmaps and search stay in the arena for the job's life), the
 //     copy of its shifts and search status word to a pinned slot buffer, and a
@@ -42,6 +48,7 @@ using mtb::round_up;
 using Arena = mtb::Arena<MTB_SERVER_MAX_SLOTS>;  // at most `slots` jobs hold memory
 
 constexpr int kRunning = 1;  // job status while queued or on the GPU
+
 
 struct Job {
     uint64_t id = 0;
@@ -79,6 +86,7 @@ struct mtb_server {
     std::unique_ptr<Arena> arena;
     uint8_t *arena_base = nullptr;
     SlotResult *results = nullptr;  // pinned, one per slot
+    SlotResult *results_dev = nullptr;  // the same area as the device addresses it (null: copy engines)
     std::vector<SlotCtx> ctx;
     std::vector<cudaStream_t> compute, copy;
     std::vector<cudaEvent_t> copied;  // [slot][copy stream]
@@ -138,11 +146,17 @@ int enqueue_job(mtb_server *s, const Job &job) {
     int32_t *d_shifts = reinterpret_cast<int32_t *>(ws + job.layout.total_bytes);
     // the copy in, in C parts of whole 256-byte units
     const size_t part = round_up((img_bytes + C - 1) / C, kArenaAlign);
+    const uint8_t *view = mtb::host_device_view(job.desc.host_images);
     for (int c = 0; c < C; ++c) {
         const size_t lo = std::min(img_bytes, part * c), hi = std::min(img_bytes, part * (c + 1));
-        if (hi > lo && cudaMemcpyAsync(d_img + lo, job.desc.host_images + lo, hi - lo, cudaMemcpyHostToDevice,
-                                       s->copy[c]) != cudaSuccess)
-            return MTB_ERR_CUDA;
+        if (hi > lo) {
+            if (view) {
+                if (mtb::launch_copy_in(view + lo, d_img + lo, hi - lo, s->copy[c]) != cudaSuccess) return MTB_ERR_CUDA;
+            } else if (cudaMemcpyAsync(d_img + lo, job.desc.host_images + lo, hi - lo, cudaMemcpyHostToDevice,
+                                       s->copy[c]) != cudaSuccess) {
+                return MTB_ERR_CUDA;
+            }
+        }
         cudaEvent_t ev = s->copied[slot * C + c];
         if (cudaEventRecord(ev, s->copy[c]) != cudaSuccess || cudaStreamWaitEvent(st, ev, 0) != cudaSuccess)
             return MTB_ERR_CUDA;
@@ -152,12 +166,18 @@ int enqueue_job(mtb_server *s, const Job &job) {
                                       job.layout.total_bytes, st);
     if (rc != MTB_OK) return rc;
     SlotResult *r = &s->results[slot];
-    if (cudaMemcpyAsync(&r->status, ws + job.layout.status_offset, sizeof(int32_t), cudaMemcpyDeviceToHost, st) !=
-            cudaSuccess ||
-        cudaMemcpyAsync(r->shifts, d_shifts, (size_t)job.desc.n_exposures * 2 * sizeof(int32_t),
-                        cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaLaunchHostFunc(st, job_done, &s->ctx[slot]) != cudaSuccess)
+    SlotResult *rd = s->results_dev ? s->results_dev + slot : nullptr;
+    if (rd) {
+        if (mtb::launch_copy_out(reinterpret_cast<const int32_t *>(ws + job.layout.status_offset), &rd->status, 1,
+                                 d_shifts, rd->shifts, job.desc.n_exposures * 2, st) != cudaSuccess)
+            return MTB_ERR_CUDA;
+    } else if (cudaMemcpyAsync(&r->status, ws + job.layout.status_offset, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                               st) != cudaSuccess ||
+               cudaMemcpyAsync(r->shifts, d_shifts, (size_t)job.desc.n_exposures * 2 * sizeof(int32_t),
+                               cudaMemcpyDeviceToHost, st) != cudaSuccess) {
         return MTB_ERR_CUDA;
+    }
+    if (cudaLaunchHostFunc(st, job_done, &s->ctx[slot]) != cudaSuccess) return MTB_ERR_CUDA;
     return MTB_OK;
 }
 
@@ -257,9 +277,14 @@ int mtb_server_create(const mtb_server_config_t *config, mtb_server_t **out) {
     if (rc == MTB_OK && cudaMalloc(&p, s->cfg.budget_bytes) != cudaSuccess) rc = MTB_ERR_OOM;
     s->arena_base = static_cast<uint8_t *>(p);
     p = nullptr;
-    if (rc == MTB_OK && cudaHostAlloc(&p, sizeof(SlotResult) * S, cudaHostAllocDefault) != cudaSuccess)
+    if (rc == MTB_OK && cudaHostAlloc(&p, sizeof(SlotResult) * S, cudaHostAllocMapped) != cudaSuccess)
         rc = MTB_ERR_OOM;
     s->results = static_cast<SlotResult *>(p);
+    if (rc == MTB_OK) {
+        void *d = nullptr;
+        if (cudaHostGetDevicePointer(&d, p, 0) == cudaSuccess) s->results_dev = static_cast<SlotResult *>(d);
+        else cudaGetLastError();
+    }
     for (int k = 0; rc == MTB_OK && k < S; ++k) {
         cudaStream_t st;
         if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) rc = MTB_ERR_CUDA;

@@ -96,6 +96,25 @@ def test_mix_matches_alone_and_oracle(mtb_lib, oracle_mod):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("copies", [1, 3])
+def test_pinned_and_pageable_inputs_agree(mtb_lib, copies):
+    """Page-locked inputs are read by the server's copy kernel, pageable ones by
+    cudaMemcpyAsync; both give the alone result (sizes with and without a
+    ragged last 16 bytes, split over one and three copy streams)."""
+    jobs = _jobs()
+    alone = _alone(mtb_lib, jobs)
+    with mtb_lib.Server(1 << 30, slots=4, copy_streams=copies) as srv:
+        ids = []
+        for k, (im, L, ref) in enumerate(jobs):
+            ids.append((k, srv.submit(im, L, 4, ref)))
+            ids.append((k, srv.submit(im.clone(), L, 4, ref)))  # a clone is pageable
+        got = [(k, srv.wait(i)[0]) for k, i in ids]
+    assert not jobs[0][0].clone().is_pinned()
+    for k, g in got:
+        assert torch.equal(g, alone[k]), k
+
+
+@pytest.mark.gpu
 def test_arrivals_while_others_run(mtb_lib):
     """Jobs submitted from another thread at random times, with the same stack
     several times in flight at once: every copy gives the alone result."""
