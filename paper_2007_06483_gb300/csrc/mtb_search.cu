@@ -87,10 +87,14 @@ k_search_items(const mtb_layout_t L, uint8_t *__restrict__ ws, const SearchPlan 
 }
 
 // Clears the error counters, the queue head, the done counters and the status
-// word of a search, then waits for the previous launch, so that the search
-// launched after it also sees the bit planes complete.
+// word of a search.  Launched chained behind whatever the stream ran before, so
+// its launch overlaps that kernel's end; it waits for that kernel before it
+// writes anything (a previous search on the same workspace may still be
+// running), and lets the search launch at once: the search waits for it in
+// turn, so it also sees the bit planes complete.
 __global__ void k_clear_search(const mtb_layout_t L, uint8_t *__restrict__ ws, int ref) {
     pdl_trigger();
+    pdl_wait();
     uint32_t *errs = reinterpret_cast<uint32_t *>(ws + L.errs_offset);
     for (int k = threadIdx.x; k < L.n * L.levels * 9; k += blockDim.x) errs[k] = 0;
     for (int k = threadIdx.x; k < L.levels * 2; k += blockDim.x) {  // the reference's rows are zero
@@ -102,17 +106,25 @@ __global__ void k_clear_search(const mtb_layout_t L, uint8_t *__restrict__ ws, i
     uint32_t *tab = reinterpret_cast<uint32_t *>(ws + L.table_offset);
     for (int k = threadIdx.x; k < L.n * kTableWords; k += blockDim.x) tab[k] = 0;
     if (threadIdx.x == 0) *status_word(ws, L) = 0;
-    pdl_wait();
 }
 
 // The staged search (mtb_search_staged.cuh).  kOverlap as for k_search_items.
 // One CTA per SM: 768 threads and the staging buffers in shared memory.
 template <bool kOverlap>
 __global__ void __launch_bounds__(kStThreads, 1)
-k_search_staged(const mtb_layout_t L, uint8_t *__restrict__ ws, const StagedPlan P) {
+k_search_staged(const mtb_layout_t Lp, uint8_t *__restrict__ ws, const StagedPlan Pp) {
     extern __shared__ __align__(128) uint8_t st_dyn[];
     __shared__ StagedShared s;
+    // the layout and the plan in shared memory: the chain reads their
+    // per-level fields at every level, by a level index only known at run time
+    __shared__ mtb_layout_t L;
+    __shared__ StagedPlan P;
+    static_assert(sizeof(mtb_layout_t) % 4 == 0 && sizeof(StagedPlan) % 4 == 0, "copied as 32-bit words");
     const int tid = threadIdx.x;
+    for (int v = tid; v < (int)(sizeof(mtb_layout_t) / 4); v += kStThreads)
+        reinterpret_cast<uint32_t *>(&L)[v] = reinterpret_cast<const uint32_t *>(&Lp)[v];
+    for (int v = tid; v < (int)(sizeof(StagedPlan) / 4); v += kStThreads)
+        reinterpret_cast<uint32_t *>(&P)[v] = reinterpret_cast<const uint32_t *>(&Pp)[v];
     if (tid == 0) {
         for (int k = 0; k < kMbCount; ++k)
             mbar_init_n(smem_addr(&s.mbar[k]), k == kMbCounted || k == kMbCounted + 1 ? kStCountWarps : 1);
@@ -376,12 +388,12 @@ int plan_staged_search(const mtb_layout_t &L, int ref_idx, int cluster, int clus
         const int halo = l == top ? 1 : kStHalo;
         return (2ll * cl_band(l) + 2 * halo) * row_bytes(l) + kStGuard <= kStBufBytes;
     };
-    // deep levels: copied whole at the pair's start
+    // deep levels: both planes copied whole at the pair's start
     int ld = L.levels;
     long long deep = 0;
     while (ld > 0) {
         const int l = ld - 1;
-        const long long bytes = ((long long)cl_band(l) + L.height[l]) * row_bytes(l);
+        const long long bytes = 2ll * L.height[l] * row_bytes(l);
         if (deep + bytes > kStDeepBytes) break;
         P.deep_off[l] = (int)deep;
         deep += bytes;
@@ -405,7 +417,7 @@ int plan_staged_search(const mtb_layout_t &L, int ref_idx, int cluster, int clus
     P.ls = ls;
     P.ld = ld < ls ? ls : ld;
     for (int l = ls; l < L.levels; ++l) {
-        P.band[l] = cl_band(l);
+        P.band[l] = l >= P.ld ? L.height[l] : cl_band(l);
         P.seg[l] = seg_rows(P.band[l], L.bits_pitch[l], kStThreads);
     }
     // grid levels: bands of one pair's rows; the first grid level is sized so
@@ -454,7 +466,7 @@ cudaError_t launch_items(const mtb_layout_t &L, int ref_idx, uint8_t *ws, int32_
     const int grid = (int)(P.total_items < cap ? P.total_items : cap);
     if (overlap)  // the pyramid stage of the same call cleared the search's areas
         return launch_k(k_search_items<true>, dim3(grid), dim3(kSearchThreads), s, true, L, ws, P);
-    cudaError_t err = launch_k(k_clear_search, dim3(1), dim3(1024), s, chained, L, ws, ref_idx);
+    cudaError_t err = launch_k(k_clear_search, dim3(1), dim3(1024), s, true, L, ws, ref_idx);
     if (err != cudaSuccess) return err;
     return launch_k(k_search_items<false>, dim3(grid), dim3(kSearchThreads), s, true, L, ws, P);
 }
@@ -506,7 +518,7 @@ cudaError_t launch_search_ex(const mtb_layout_t &L, int ref_idx, uint8_t *ws, in
                             withhold_pair, overlap, chain);
     last_status_slot(s, true, &P.status_out);
     if (!overlap) {
-        err = launch_k(k_clear_search, dim3(1), dim3(1024), s, chained, L, ws, ref_idx);
+        err = launch_k(k_clear_search, dim3(1), dim3(1024), s, true, L, ws, ref_idx);
         if (err != cudaSuccess) return err;
     }
     cudaLaunchConfig_t cfg = {};

@@ -16,11 +16,14 @@
 //     4 s_(l+2) away from the reference rows.  That superset is copied into
 //     shared memory (one bulk copy of whole rows, completion on an mbarrier)
 //     while level l + 1 is still being counted.
-//   - Every pair's deep levels run on one thread-block cluster.  Each CTA counts
-//     one band of reference rows, pushes its 9 partial counts into every CTA of
-//     the cluster (distributed shared memory) and meets the others at the
-//     cluster barrier; every CTA then takes the same argmin, so nothing needs
-//     broadcasting.  The deepest levels are copied whole at the pair's start.
+//   - Every pair's coarse levels run on one thread-block cluster.  At a cluster
+//     level each CTA counts one band of reference rows, pushes its 9 partial
+//     counts into every CTA of the cluster (distributed shared memory) and
+//     meets the others at the cluster barrier; every CTA then takes the same
+//     argmin, so nothing needs broadcasting.  The deepest levels (a few KB) are
+//     copied whole at the pair's start and counted whole by every CTA of the
+//     cluster, with a reduction inside the CTA: the same counts, hence the
+//     same argmin, in every CTA with no exchange between them.
 //   - The largest levels are spread over every CTA of the grid as tasks (one
 //     band of reference rows of one pair) taken from a queue in level order.
 //     A CTA holds two tasks, one per staging buffer: the second one's rows are
@@ -59,13 +62,15 @@ struct StagedPlan {
     int ref, pairs, chain;
     int cluster;  // CTAs per cluster
     int ls;       // levels >= ls run on the pair's cluster, levels < ls on the grid
-    int ld;       // levels >= ld (cluster levels) are copied whole at the pair's start
+    int ld;       // levels >= ld (the deep levels) are copied whole at the pair's start and
+                  // counted whole by every CTA of the cluster
     // per level: reference rows of one band (cluster levels: one CTA's band;
-    // grid levels: one task's band) and the rows one thread walks
+    // deep levels: the whole level; grid levels: one task's band) and the rows
+    // one thread walks
     int band[MTB_MAX_LEVELS], seg[MTB_MAX_LEVELS];
     int tasks[MTB_MAX_LEVELS];       // grid levels: tasks (bands) per pair
     int first_task[MTB_MAX_LEVELS];  // grid levels: queue index of pair 0's band 0
-    int deep_off[MTB_MAX_LEVELS];    // deep levels: byte offset in the deep area (ref band, then the whole plane of i)
+    int deep_off[MTB_MAX_LEVELS];    // deep levels: byte offset in the deep area (the whole plane of ref, then of i)
     int total_tasks;                 // grid tasks plus the final task
     int bit_chunk_words;
     int withhold_pair;  // test hook: this pair's cluster work never reports completion (-1: none)
@@ -107,7 +112,8 @@ struct StagedShared {
     uint32_t acc[2][9], prev[2][9];
     uint32_t arrived[2];
     uint32_t slot[2][kStMaxCluster][9];
-    uint32_t part[2][kStWarps][9];       // grid: each counting warp's counts of the task in buffer b
+    uint32_t part[2][kStWarps][9];       // grid: each counting warp's counts of the task in buffer b;
+                                         // deep levels: each warp's counts, by level parity
     StagedTask desc[2];                  // grid: the task in buffer b
     int cache_key[kStCache];             // grid: (pair, level) whose choice is known, -1 none
     int2 cache_val[kStCache];
@@ -474,35 +480,29 @@ __device__ void st_pair(const mtb_layout_t &L, uint8_t *ws, const StagedPlan &P,
     const int i = st_exposure(P, p), r = st_pair_ref(P, i);
     int32_t *status = status_word(ws, L);
     uint8_t *deep = dyn + 2 * kStBufBytes;
-    // the deep levels: this CTA's reference band and the whole plane of exposure i
+    // the deep levels: the whole planes of the reference and of exposure i
     if (tid == 0 && P.ld < L.levels) {
         for (int l = L.levels - 1; l >= P.ld; --l) st_wait_plane<kOverlap>(ws, L, P, r, l);
         for (int l = L.levels - 1; l >= P.ld; --l) st_wait_plane<kOverlap>(ws, L, P, i, l);
         uint32_t bytes = 0;
-        for (int l = L.levels - 1; l >= P.ld; --l) {
-            const int bp = L.bits_pitch[l], hl = L.height[l];
-            const int y0 = min(hl, rank * P.band[l]), y1 = min(hl, y0 + P.band[l]);
-            bytes += (uint32_t)(y1 - y0 + hl) * (uint32_t)bp * 8u;
-        }
+        for (int l = L.levels - 1; l >= P.ld; --l) bytes += 2u * (uint32_t)L.height[l] * (uint32_t)L.bits_pitch[l] * 8u;
         const uint32_t mb = smem_addr(&s.mbar[kMbDeep]);
         mbar_arrive_tx(mb, bytes);
         for (int l = L.levels - 1; l >= P.ld; --l) {
-            const int bp = L.bits_pitch[l], hl = L.height[l];
-            const int y0 = min(hl, rank * P.band[l]), y1 = min(hl, y0 + P.band[l]);
+            const uint32_t pb = (uint32_t)L.height[l] * (uint32_t)L.bits_pitch[l] * 8u;
             uint8_t *dst = deep + P.deep_off[l];
-            const uint32_t rb = (uint32_t)(y1 - y0) * (uint32_t)bp * 8u;
-            if (rb) bulk_g2s(smem_addr(dst), Planes::bits(ws, L, r, l) + (size_t)y0 * bp, rb, mb);
-            bulk_g2s(smem_addr(dst + rb), Planes::bits(ws, L, i, l), (uint32_t)hl * (uint32_t)bp * 8u, mb);
+            bulk_g2s(smem_addr(dst), Planes::bits(ws, L, r, l), pb, mb);
+            bulk_g2s(smem_addr(dst + pb), Planes::bits(ws, L, i, l), pb, mb);
         }
     }
     bool deep_pending = P.ld < L.levels;
     int bx = 0, by = 0;
     for (int l = L.levels - 1; l >= P.ls; --l) {
         const int bp = L.bits_pitch[l], hl = L.height[l];
-        const int y0 = min(hl, rank * P.band[l]), y1 = min(hl, y0 + P.band[l]);
         const bool is_deep = l >= P.ld;
+        const int y0 = is_deep ? 0 : min(hl, rank * P.band[l]), y1 = is_deep ? hl : min(hl, y0 + P.band[l]);
         const int b = l & 1;
-        const int q = lv & 1;  // this level's exchange barrier, sums and slots
+        const int q = lv & 1;  // this (cluster) level's exchange barrier, sums and slots
         if (tid == 0) {
             // level l itself when no earlier level could stage it (the deepest
             // level when it is not copied whole: its base is 0), then level
@@ -528,8 +528,8 @@ __device__ void st_pair(const mtb_layout_t &L, uint8_t *ws, const StagedPlan &P,
                 st_copy_rows(Planes::bits(ws, L, i, n), bpn, hn, lo, hi, buf + st_exp_offset(z1 - z0, bpn),
                              smem_addr(&s.mbar[kMbExp + bn]), &rows);
             }
-            // this level's exchange: 9 words from every rank
-            mbar_arrive_tx(smem_addr(&s.mbar[kMbLvl + q]), (uint32_t)(36 * C));
+            // a cluster level's exchange: 9 words from every rank
+            if (!is_deep) mbar_arrive_tx(smem_addr(&s.mbar[kMbLvl + q]), (uint32_t)(36 * C));
         }
         const uint2 *sref, *sexp;
         int ea, ne;
@@ -539,7 +539,7 @@ __device__ void st_pair(const mtb_layout_t &L, uint8_t *ws, const StagedPlan &P,
                 deep_pending = false;
             }
             sref = reinterpret_cast<const uint2 *>(deep + P.deep_off[l]);
-            sexp = sref + (size_t)(y1 - y0) * bp;
+            sexp = sref + (size_t)hl * bp;
             ea = 0;
             ne = hl;
         } else {
@@ -558,12 +558,29 @@ __device__ void st_pair(const mtb_layout_t &L, uint8_t *ws, const StagedPlan &P,
                 st_count_staged(sref, sexp, y1 - y0, ea, ne, bp, (L.width[l] + 31) >> 5, y0, bx, by, P.seg[l], tid,
                                 kStThreads, cnt);
         }
-        st_exchange(s, cnt, q, rank, C, lane);
-        // every warp: the level's totals and their argmin
-        mbar_wait(s, kMbLvl + q, ph, status, P.timeout_ns);
         uint32_t e = 0;
-        if (lane < 9)
-            for (int k = 0; k < C; ++k) e += s.slot[q][k][lane];
+        if (is_deep) {
+            // the whole level in this CTA: each warp's 9 sums, one barrier, and
+            // lane k of every warp adds candidate k over the warps (the buffer
+            // of this level's parity is written again two levels on, after the
+            // next level's barrier)
+            uint32_t v = 0;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                const uint32_t t = __reduce_add_sync(0xffffffffu, cnt[k]);
+                if (lane == k) v = t;
+            }
+            if (lane < 9) s.part[b][tid >> 5][lane] = v;
+            __syncthreads();
+            if (lane < 9)
+                for (int w = 0; w < kStWarps; ++w) e += s.part[b][w][lane];
+        } else {
+            st_exchange(s, cnt, q, rank, C, lane);
+            // every warp: the level's totals and their argmin
+            mbar_wait(s, kMbLvl + q, ph, status, P.timeout_ns);
+            if (lane < 9)
+                for (int k = 0; k < C; ++k) e += s.slot[q][k][lane];
+        }
         uint32_t ev[9];
 #pragma unroll
         for (int k = 0; k < 9; ++k) ev[k] = __shfl_sync(0xffffffffu, e, k);
@@ -580,7 +597,7 @@ __device__ void st_pair(const mtb_layout_t &L, uint8_t *ws, const StagedPlan &P,
         }
         bx = 2 * sx;
         by = 2 * sy;
-        ++lv;
+        if (!is_deep) ++lv;
     }
 }
 
