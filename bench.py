@@ -27,7 +27,11 @@ The default line also carries a compact batched-vs-plain record (`batch`): the
 uneven stacks of the batched form (--batch-count of them, 256 by default) in
 one persistent launch against the plain path on the same stacks, with every
 stack's shifts and per-level errors compared with the oracle (run on every
-usable host core, outside the timed regions).
+usable host core, outside the timed regions), and a compact served record
+(`serve`): a short run of the serving loop (--serve-pool distinct 6000x4000x7
+jobs, 64 Poisson arrivals at each of 10, 100 and 1000 jobs/s offered) with
+p50/p99 latency per rate, the served MPix/s against the plain path on the same
+jobs, and every served job's shifts compared with the oracle's.
 
 Inputs and workspaces rotate over several device copies, so between two uses of
 one buffer more than 3x the L2 capacity is written and read: every step starts
@@ -125,6 +129,8 @@ def parse_args(argv=None):
     p.add_argument("--slots", type=int, default=8, help="serve: jobs on the GPU at most")
     p.add_argument("--copy-streams", type=int, default=1, help="serve: copy streams per job")
     p.add_argument("--budget-gb", type=float, default=40.0, help="serve: device-memory budget")
+    p.add_argument("--serve-pool", type=int, default=8,
+                   help="default workload: jobs of the short served run folded into the line (0: none)")
     return p.parse_args(argv)
 
 
@@ -683,6 +689,14 @@ def run_gb300(args):
         batch = batch_record(args.batch_count, dev, stream, args.warmup, 5,
                              oracle_check=not args.no_cpu_baseline)
 
+    serve = None
+    if rank == 0 and world == 1 and args.serve_pool > 0:
+        # a short served run (10, 100 and 1000 jobs/s offered, 64 jobs each)
+        # of 6000x4000x7 jobs, every result checked against the oracle
+        sargs = argparse.Namespace(**vars(args))
+        sargs.pool, sargs.rates = args.serve_pool, "10,100,1000"
+        serve = serve_summary(serve_line(sargs, max_jobs=64, probe=False))
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": K,
@@ -699,6 +713,7 @@ def run_gb300(args):
             "cpu_baseline_threaded": cpu_threaded,
             "e2e": e2e,
             "batch": batch,
+            "serve": serve,
             "gpu_launches": K * regions * kernels_per_step(spec),
             "clocks": clocks,
             "planted_shifts_recovered": planted_ok,
@@ -871,12 +886,16 @@ def h2d_copy_probe(pool, dev, stream, count: int = 40, gap_s: float = 0.02) -> d
 
 
 def run_serve(args):
+    print(json.dumps(serve_line(args)), flush=True)
+
+
+def serve_line(args, max_jobs: int = 500, probe: bool = True) -> dict:
     """Poisson arrivals of 6000x4000x7 jobs (synth.serve_specs, pinned host
     memory) into the serving loop under a device-memory budget, swept over the
-    offered rates.  Latency runs from a job's scheduled arrival to its shifts
-    being in host memory (copy in over NVLink-C2C, alignment, copy out).  Every
-    served result is compared with the same job aligned alone on the plain
-    path."""
+    offered rates (at most max_jobs jobs a rate).  Latency runs from a job's
+    scheduled arrival to its shifts being in host memory (copy in over
+    NVLink-C2C, alignment, copy out).  Every served result is compared with the
+    same job aligned alone on the plain path and with the oracle's answer."""
     import threading
 
     import numpy as np
@@ -924,7 +943,7 @@ def run_serve(args):
     del resident, ws, outp
     torch.cuda.empty_cache()
     link_gbs = h2d_link_gbs(pool[0], dev, stream)
-    copy_probe = h2d_copy_probe(pool, dev, stream)
+    copy_probe = h2d_copy_probe(pool, dev, stream) if probe else None
     sp0 = specs[0]
     px = sp0.aligned_pixels
     job_bytes = mtb.job_bytes(sp0.n, sp0.w, sp0.h, sp0.levels, sp0.noise_tol, sp0.ref)
@@ -939,7 +958,7 @@ def run_serve(args):
             srv.wait(srv.submit(pool[k % len(pool)], sp0.levels, sp0.noise_tol, sp0.ref))
         sampler.start()
         for rate in rates:
-            count = int(max(64, min(500, rate * 3)))
+            count = int(min(max_jobs, max(64, min(500, rate * 3))))
             gaps = rng.exponential(1.0 / rate, count)
             sched = np.cumsum(gaps) - gaps[0]
             picks = [k % len(pool) for k in range(count)]
@@ -1034,7 +1053,28 @@ def run_serve(args):
         "planted_shifts_recovered": f"{planted}/{len(specs)} jobs",
         "gpu_launches": kernels_per_step(sp0) * sum(r["jobs"] for r in results), "clocks": clocks,
     }
-    print(json.dumps(line), flush=True)
+    del pool, srv
+    torch.cuda.empty_cache()
+    return line
+
+
+def serve_summary(line: dict) -> dict:
+    """The served form in brief, for the default line: per offered rate the
+    served rate, latency and the equality counts, and the best served MPix/s
+    against the plain path on the same jobs."""
+    best = line["value"]
+    plain = line["plain_path_device_resident"]["mpix_s"]
+    return {
+        "workload": line["config"]["workload"], "pool_jobs": line["config"]["pool_jobs"],
+        "slots": line["config"]["slots"], "budget_gb": line["config"]["budget_gb"],
+        "value": best, "unit": line["unit"], "plain_device_resident_mpix_s": plain,
+        "served_vs_plain": round(best / plain, 4) if plain else None,
+        "h2d_link_frac": line["roofline"]["frac"],
+        "rates": [{k: r[k] for k in ("offered_jobs_s", "jobs", "served_jobs_s", "mpix_s", "p50_ms", "p99_ms",
+                                      "same_as_alone", "oracle_equal")} for r in line["serving"]],
+        "alone_equal_oracle": line["alone_equal_oracle"], "oracle_check": line["oracle_check"],
+        "server_stats": line["server_stats"],
+    }
 
 
 # ----------------------------------------------------------------------------- after the alignment

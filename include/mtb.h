@@ -221,7 +221,10 @@ size_t mtb_host_workspace_bytes(int n_exposures, int w, int h, int levels);
  * 16 MB each) on a copy stream the library owns, one per device; the pyramid
  * pass over each band runs on `stream` as soon as the band has landed, after
  * work enqueued earlier on `stream`.  Smaller stacks are copied in one piece on
- * `stream`.  The alignment and the copy out are enqueued on `stream`, and the
+ * `stream`, by a copy kernel when host_images is page-locked and 16-byte
+ * aligned (a copy engine idle for some milliseconds is slow to start), else by
+ * cudaMemcpyAsync; page-locked host_shifts_out is written by SM stores.  The
+ * alignment and the copy out are enqueued on `stream`, and the
  * call returns after synchronising it.  device_workspace: device, 256-byte
  * aligned, >= mtb_host_workspace_bytes(...) bytes, or NULL to allocate
  * stream-ordered.  Thread-safe; calls from several threads share the copy

@@ -249,19 +249,18 @@ int enqueue_banded(const uint8_t *host_images, uint8_t *d_img, const mtb_layout_
         cudaStreamSynchronize(p->copy);
         return MTB_ERR_CUDA;
     };
-    // page-locked images are read by the copy kernel, the rest (and bands that
-    // start off a 16-byte boundary) by the copy engine
-    const uint8_t *view = host_device_view(host_images);
+    // the bands go through the copy engine: a copy kernel would wait for SMs
+    // held by the previous band's pyramid pass, so the copy and the pyramid
+    // would no longer overlap (6000x4000x7 end to end: 2.85 ms with the copy
+    // kernel, 2.62 ms with the copy engine)
     int k = 0;
     for (int e = 0; e < L.n; ++e)
         for (int b = 0; b < bands; ++b, ++k) {
             const long long r0 = tile_rows * b / bands, r1 = tile_rows * (b + 1) / bands;
             const size_t y0 = (size_t)r0 * kTileRows, y1 = (size_t)(r1 * kTileRows < L.h ? r1 * kTileRows : L.h);
             const size_t off = ((size_t)e * L.h + y0) * row_bytes, len = (y1 - y0) * row_bytes;
-            const cudaError_t err = view && (off & 15) == 0
-                                        ? launch_copy_in(view + off, d_img + off, len, p->copy)
-                                        : cudaMemcpyAsync(d_img + off, host_images + off, len, cudaMemcpyHostToDevice,
-                                                          p->copy);
+            const cudaError_t err =
+                cudaMemcpyAsync(d_img + off, host_images + off, len, cudaMemcpyHostToDevice, p->copy);
             if (err != cudaSuccess || cudaEventRecord(p->band[k], p->copy) != cudaSuccess) return fail();
         }
     if (launch_clear_stack(L, ws, s) != cudaSuccess) return fail();
