@@ -238,7 +238,7 @@ int enqueue_banded(const uint8_t *host_images, uint8_t *d_img, const mtb_layout_
     if (!p) return MTB_ERR_CUDA;
     std::lock_guard<std::mutex> g(p->mu);
     const long long tile_rows = (L.h + kTileRows - 1) / kTileRows;
-    const long long tiles_x = (L.w + kTileCols - 1) / kTileCols;
+    const long long tiles_x = pyramid_tiles_x(L);
     const long long per_exp = pyramid_tiles_per_exposure(L);
     const size_t row_bytes = (size_t)L.w * 3;
     // the copy must not overwrite the device images while earlier work on s

@@ -112,6 +112,9 @@ cudaError_t launch_pyramid(const uint8_t *images, const mtb_layout_t &L, uint8_t
 // pyramid pass over tiles [tile_begin, tile_end) (tile t is tile t % per_exp,
 // row-major, of exposure t / per_exp; launch_pyramid covers them all).
 cudaError_t launch_clear_stack(const mtb_layout_t &L, uint8_t *ws, cudaStream_t s);
+// Tiles of one 32-row tile row (widths a multiple of 16: 32 x 512 units of
+// two 16 x 512 tiles; other widths: 32 x 256 tiles), and of one exposure.
+int pyramid_tiles_x(const mtb_layout_t &L);
 long long pyramid_tiles_per_exposure(const mtb_layout_t &L);
 cudaError_t launch_pyramid_range(const uint8_t *images, const mtb_layout_t &L, uint8_t *ws, long long tile_begin,
                                  long long tile_end, cudaStream_t s, bool chained);
