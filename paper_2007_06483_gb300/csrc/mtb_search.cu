@@ -418,7 +418,7 @@ int plan_staged_search(const mtb_layout_t &L, int ref_idx, int cluster, int clus
     P.ld = ld < ls ? ls : ld;
     for (int l = ls; l < L.levels; ++l) {
         P.band[l] = l >= P.ld ? L.height[l] : cl_band(l);
-        P.seg[l] = seg_rows(P.band[l], L.bits_pitch[l], kStThreads);
+        P.seg[l] = seg_rows(P.band[l], L.bits_pitch[l], l >= P.ld ? kStSoloThreads : kStThreads);
     }
     // grid levels: bands of one pair's rows; the first grid level is sized so
     // that the CTAs not running a pair hold all of it, two tasks each

@@ -23,7 +23,9 @@
 //     argmin, so nothing needs broadcasting.  The deepest levels (a few KB) are
 //     copied whole at the pair's start and counted whole by every CTA of the
 //     cluster, with a reduction inside the CTA: the same counts, hence the
-//     same argmin, in every CTA with no exchange between them.
+//     same argmin, in every CTA with no exchange between them.  Only the first
+//     kStSoloWarps warps run them; the others wait for their base at the first
+//     cluster level.
 //   - The largest levels are spread over every CTA of the grid as tasks (one
 //     band of reference rows of one pair) taken from a queue in level order.
 //     A CTA holds two tasks, one per staging buffer: the second one's rows are
@@ -43,6 +45,11 @@ namespace mtb {
 
 constexpr int kStThreads = 768;  // one CTA per SM (shared memory), 84 registers at most
 constexpr int kStWarps = kStThreads / 32;
+// the deep levels run on the first kStSoloWarps warps only (named barrier 1):
+// a level of a few KB has too little work for 24 warps, and every warp that
+// takes part runs the level's reduction and argmin
+constexpr int kStSoloWarps = 8;
+constexpr int kStSoloThreads = kStSoloWarps * 32;
 constexpr int kStMaxCluster = 16;
 constexpr int kStBufBytes = 98 * 1024;  // each of the two staging buffers
 constexpr int kStDeepBytes = 24 * 1024;  // the deep levels of one pair
@@ -118,6 +125,7 @@ struct StagedShared {
     int cache_key[kStCache];             // grid: (pair, level) whose choice is known, -1 none
     int2 cache_val[kStCache];
     int task;                            // the pair a cluster draws (rank 0's word)
+    int solo_base[2];                    // the base the deep levels leave for the first cluster level
     int ea[2], ne[2];                    // cluster levels: first exposure row staged in buffer b, rows
 };
 
@@ -496,10 +504,17 @@ __device__ void st_pair(const mtb_layout_t &L, uint8_t *ws, const StagedPlan &P,
         }
     }
     bool deep_pending = P.ld < L.levels;
+    const bool solo = tid < kStSoloThreads;
     int bx = 0, by = 0;
     for (int l = L.levels - 1; l >= P.ls; --l) {
         const int bp = L.bits_pitch[l], hl = L.height[l];
         const bool is_deep = l >= P.ld;
+        if (is_deep && !solo) continue;  // these warps wait for the deep levels' base below
+        if (l == P.ld - 1 && P.ld < L.levels) {
+            __syncthreads();  // the deep levels are done: every warp takes their base
+            bx = s.solo_base[0];
+            by = s.solo_base[1];
+        }
         const int y0 = is_deep ? 0 : min(hl, rank * P.band[l]), y1 = is_deep ? hl : min(hl, y0 + P.band[l]);
         const int b = l & 1;
         const int q = lv & 1;  // this (cluster) level's exchange barrier, sums and slots
@@ -553,7 +568,7 @@ __device__ void st_pair(const mtb_layout_t &L, uint8_t *ws, const StagedPlan &P,
         uint32_t cnt[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
         if (y1 > y0) {
             if (is_deep)
-                st_count_any(sref, sexp, y1 - y0, ea, ne, bp, y0, bx, by, P.seg[l], tid, kStThreads, cnt);
+                st_count_any(sref, sexp, y1 - y0, ea, ne, bp, y0, bx, by, P.seg[l], tid, kStSoloThreads, cnt);
             else
                 st_count_staged(sref, sexp, y1 - y0, ea, ne, bp, (L.width[l] + 31) >> 5, y0, bx, by, P.seg[l], tid,
                                 kStThreads, cnt);
@@ -571,9 +586,10 @@ __device__ void st_pair(const mtb_layout_t &L, uint8_t *ws, const StagedPlan &P,
                 if (lane == k) v = t;
             }
             if (lane < 9) s.part[b][tid >> 5][lane] = v;
-            __syncthreads();
+            asm volatile("bar.sync 1, %0;" ::"n"(kStSoloThreads) : "memory");
             if (lane < 9)
-                for (int w = 0; w < kStWarps; ++w) e += s.part[b][w][lane];
+#pragma unroll
+                for (int w = 0; w < kStSoloWarps; ++w) e += s.part[b][w][lane];
         } else {
             st_exchange(s, cnt, q, rank, C, lane);
             // every warp: the level's totals and their argmin
@@ -598,6 +614,10 @@ __device__ void st_pair(const mtb_layout_t &L, uint8_t *ws, const StagedPlan &P,
         bx = 2 * sx;
         by = 2 * sy;
         if (!is_deep) ++lv;
+        if (is_deep && l == P.ld && tid == 0) {
+            s.solo_base[0] = bx;
+            s.solo_base[1] = by;
+        }
     }
 }
 
@@ -768,43 +788,43 @@ __device__ void st_final(const mtb_layout_t &L, uint8_t *ws, const StagedPlan &P
     }
     ok = __shfl_sync(0xffffffffu, ok, 0);
     if (!ok) return;
-    // the lanes split the (exposure, level) items, so the reads of different
-    // items are in flight together; level 0's shift is the choice its counts
-    // make (0 for the reference)
-    const int items = L.n * L.levels;
-    for (int it = lane; it < items; it += 32) {
-        const int e = it / L.levels, l = it - e * L.levels;
-        int sx, sy;
-        if (l == 0) {
-            sx = sy = 0;
-            if (e != P.ref) {
-                const int2 c = st_choice(ws, L, e, 0);
-                sx = c.x;
-                sy = c.y;
-            }
-            int32_t *s0 = Planes::shift(ws, L, e, 0);
-            s0[0] = sx;
-            s0[1] = sy;
-            if (P.shifts_out && !P.chain) {
-                P.shifts_out[2 * e] = sx;
-                P.shifts_out[2 * e + 1] = sy;
-            }
-        } else {
-            const int32_t *sl = Planes::shift(ws, L, e, l);
-            sx = __ldcg(sl);
-            sy = __ldcg(sl + 1);
+    // level 0's shift of every exposure at once, one exposure a lane: the
+    // choice its counts make (0 for the reference)
+    for (int e = lane; e < L.n; e += 32) {
+        int sx = 0, sy = 0;
+        if (e != P.ref) {
+            const int2 c = st_choice(ws, L, e, 0);
+            sx = c.x;
+            sy = c.y;
         }
-        if (P.level_shifts_out) {
-            P.level_shifts_out[(size_t)it * 2] = sx;
-            P.level_shifts_out[(size_t)it * 2 + 1] = sy;
+        int32_t *s0 = Planes::shift(ws, L, e, 0);
+        s0[0] = sx;
+        s0[1] = sy;
+        if (P.shifts_out && !P.chain) {
+            P.shifts_out[2 * e] = sx;
+            P.shifts_out[2 * e + 1] = sy;
         }
-        if (P.level_errs_out) {
-            const uint32_t *el = Planes::errs(ws, L, e, l);
-            uint32_t v[9];
+    }
+    __syncwarp();  // the level-0 rows above are read back below
+    // the per-level outputs, when asked for: the lanes split the (exposure,
+    // level) items, so the reads of different items are in flight together
+    if (P.level_shifts_out || P.level_errs_out) {
+        const int items = L.n * L.levels;
+        for (int it = lane; it < items; it += 32) {
+            const int e = it / L.levels, l = it - e * L.levels;
+            if (P.level_shifts_out) {
+                const int32_t *sl = Planes::shift(ws, L, e, l);
+                P.level_shifts_out[(size_t)it * 2] = __ldcg(sl);
+                P.level_shifts_out[(size_t)it * 2 + 1] = __ldcg(sl + 1);
+            }
+            if (P.level_errs_out) {
+                const uint32_t *el = Planes::errs(ws, L, e, l);
+                uint32_t v[9];
 #pragma unroll
-            for (int k = 0; k < 9; ++k) v[k] = __ldcg(el + k);
+                for (int k = 0; k < 9; ++k) v[k] = __ldcg(el + k);
 #pragma unroll
-            for (int k = 0; k < 9; ++k) P.level_errs_out[(size_t)it * 9 + k] = v[k];
+                for (int k = 0; k < 9; ++k) P.level_errs_out[(size_t)it * 9 + k] = v[k];
+            }
         }
     }
     if (!P.chain || !P.shifts_out) return;
