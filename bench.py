@@ -91,15 +91,15 @@ NCU_TRAFFIC = {
     ("k_pyramid", "stack4000x3000x3"): {"bytes": 116647680, "sources_sha256": "51d50f00dfb4fe6bf0b3fbd829edfbd37d05433985f0057cd6a55eace28f9b84"},
     ("k_apply_shifts", "apply6000x4000x7"): {"bytes": 955071744, "sources_sha256": "e265c02bbfa6e0cda0bd4c35ae4a6118438da478c9b3a3a35471b1d9ce84ba18"},
     # the 6000x4000x7 stack, `bench.py --profile --steps 2 --warmup 2` under
-    # ncu, mean over the captured launches: k_pyramid 536.91 MB read + 167.51 MB
-    # written (3 launches), k_bitmaps 224.69 + 6.22 MB (3), k_search_staged
-    # 56.38 + 0.00 MB (2), k_search_items 56.33 + 0.00 MB (2). Written bytes
+    # ncu, mean over the captured launches: k_pyramid 531.88 MB read + 168.19 MB
+    # written (4 launches), k_bitmaps 224.68 + 6.11 MB (4), k_search_staged
+    # 56.38 + 0.00 MB (2), k_search_items 56.36 + 0.00 MB (2). Written bytes
     # still dirty in L2 when a launch ends are not counted, hence writes below
     # the algorithmic figure
-    ("k_pyramid", "stack6000x4000x7"): {"bytes": 704418389, "sources_sha256": "90df573d5d3294bac4d769b0160e4d7e766b85a244e1446049608932cab768bb"},
-    ("k_bitmaps", "stack6000x4000x7"): {"bytes": 230917461, "sources_sha256": "bb35a732ebbd013dbd2dcc3ec1c9480b52044fe74147e42a75467b612fb6862c"},
-    ("k_search_staged", "stack6000x4000x7"): {"bytes": 56375680, "sources_sha256": "716614be7b5266bc8dbed05da8e7af8e32025b752d9e61a500b693b8fc8857d7"},
-    ("k_search_items", "stack6000x4000x7"): {"bytes": 56334080, "sources_sha256": "d2020c4d98cdd95aec14546405557de8c1b8e067c3ed568c2f228764cd2c7a21"},
+    ("k_pyramid", "stack6000x4000x7"): {"bytes": 700065344, "sources_sha256": "4445f47163a7a5a8976c2ce3a706143b41cdd11c97a113cdd9912f3cd633c9d0"},
+    ("k_bitmaps", "stack6000x4000x7"): {"bytes": 230792704, "sources_sha256": "4d310b227589784b750c863365e8294c8c34547c80ab75c40b04052b9e717bc3"},
+    ("k_search_staged", "stack6000x4000x7"): {"bytes": 56384128, "sources_sha256": "209fd8d2243b35cd7ace413e32a231ebcc0c45ddaac4d4dbca69ed1464e28620"},
+    ("k_search_items", "stack6000x4000x7"): {"bytes": 56358656, "sources_sha256": "08531c5e990566f277033cfd7a58aed4bfcc38c8c6b0da9486d8f9c95c2f8d24"},
 }
 
 
