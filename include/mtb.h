@@ -192,7 +192,7 @@ int mtb_workspace_status(const void *workspace, size_t workspace_bytes, int n_ex
 
 /* Which of the library's two search kernels a search of this stack runs on the
  * calling thread's current device: 1 the staged kernel (bit planes staged in
- * shared memory, deep levels on thread-block clusters), 0 the item kernel
+ * shared memory, coarse levels on thread-block clusters), 0 the item kernel
  * (persistent work queue).  chained != 0: the search of a whole-stack call
  * (mtb_align_stack*), which starts while the bitmaps are still being packed;
  * 0: mtb_search_shifts on its own.  Both compute the same result (Sec. III-A,

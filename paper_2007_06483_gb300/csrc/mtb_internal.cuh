@@ -12,9 +12,11 @@ namespace mtb {
 
 // ---------------------------------------------------------------------------
 // Pyramid pass geometry.  One tile is kTileRows x kTileCols full-resolution
-// pixels; because 2^l divides both, every pixel of levels 1..kTileLog2 has its
-// whole 2^l x 2^l source block inside one tile, so a tile builds its part of
-// those levels on chip.  Deeper levels come from the bitmap pass.
+// pixels (widths a multiple of 16 use 32 x 512 units of two 16 x 512 tiles
+// instead, mtb_pyramid.cu); because 2^l divides both sides, every pixel of
+// levels 1..kTileLog2 has its whole 2^l x 2^l source block inside one tile, so
+// a tile builds its part of those levels on chip.  Deeper levels come from the
+// bitmap pass.
 constexpr int kTileLog2 = 5;
 constexpr int kTileRows = 1 << kTileLog2;  // 32
 constexpr int kTileCols = 256;

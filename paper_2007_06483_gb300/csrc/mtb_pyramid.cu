@@ -6,9 +6,11 @@
 //     level made from the previous one as in Sec. III-B),
 //   * the 256-bin histogram of each of those levels and its median (Sec. III-A,
 //     Sec. III-B).
-// A CTA owns 32-row x 256-column tiles of full-resolution pixels.  Level-l
-// pixels of a tile have their whole 2^l x 2^l source block inside it (l <= 5),
-// so the tile's part of levels 1..5 is built on chip from the gray tile.  HBM
+// A CTA owns runs of 32-row blocks of full-resolution pixels: 32 x 512 units
+// (two 16 x 512 tiles) when the width is a multiple of 16, 32 x 256 tiles
+// otherwise.  Level-l pixels of a block have their whole 2^l x 2^l source
+// block inside it (l <= 5), so the block's part of levels 1..5 is built on
+// chip from its gray.  HBM
 // traffic per full-resolution pixel: 3 bytes read (RGB) + 4/3 bytes written
 // (gray levels).
 //

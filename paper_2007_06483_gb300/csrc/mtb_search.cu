@@ -478,8 +478,10 @@ namespace {
 // Whether a search of this stack runs the staged kernel (else the item kernel).
 // The staged kernel needs whole SMs (one CTA each) in clusters: right behind
 // the bitmap pass it starts only once bitmap CTAs have left whole SMs, and the
-// item kernel, whose CTAs fit beside them, overlaps that pass better.  On its
-// own it wins from about 64 M pair-pixels at level 0 (6000x4000x7: 62.0
+// item kernel, whose CTAs fit beside them, overlaps that pass about as well
+// (6000x4000x7 one-call step: 242.4 us with the item kernel, 240.7 us with the
+// staged one; 4000x3000x3: 78.3 against 85.4 us).  On its own the staged
+// kernel wins from about 64 M pair-pixels at level 0 (6000x4000x7: 59.3
 // against 69.6 us; 4000x3000x3: 41.7 against 40.7 us).  MTB_SEARCH_ITEMS=1
 // (0) forces the item (staged) kernel, for comparisons and tests.
 bool wants_staged(const mtb_layout_t &L, bool overlap) {
