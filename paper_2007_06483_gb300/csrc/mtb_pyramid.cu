@@ -194,7 +194,8 @@ struct WideCursor {
     }
     __device__ __forceinline__ int y0() const { return uy * kUnitRows + half * kWideRows; }
     __device__ __forceinline__ int x0() const { return ux * kWideCols; }
-    // false once the run [.., u1) is done (unit index tracked in *u)
+    // to the next tile: the bottom tile of this unit when it lies inside the
+    // image, else the top tile of the next unit (*u counts the units)
     __device__ __forceinline__ void next(int units_x, int units_y, int h, int *u) {
         if (half == 0 && uy * kUnitRows + kWideRows < h) {
             half = 1;
