@@ -61,3 +61,28 @@ def test_reference_arm_times_whole_stacks(capsys):
     assert line["impl"] == "reference" and line["config"]["workload"] == "pair640x480"
     assert line["unit"] == "MPix/s" and line["value"] > 0 and line["e2e"]["value"] == line["value"]
     assert "whole pair640x480 stack" in line["cpu_baseline"]["sample"]
+
+
+def test_serve_summary_keeps_the_checked_counts():
+    """The served run folded into the default line keeps, per offered rate,
+    the latency and both equality counts, and relates the best served rate to
+    the plain path on the same jobs."""
+    rates = [{"offered_jobs_s": r, "jobs": 64, "served_jobs_s": min(r, 400.0), "mpix_s": 144.0 * min(r, 400.0),
+              "p50_ms": 2.7, "p99_ms": 5.0, "same_as_alone": "64/64", "oracle_equal": "64/64",
+              "queue_p50_ms": 0.01, "h2d_gbs": 1.0} for r in (10.0, 100.0, 1000.0)]
+    line = {"value": 57600.0, "unit": "MPix/s",
+            "config": {"workload": "serve6000x4000x7", "pool_jobs": 8, "slots": 8, "budget_gb": 40.0},
+            "plain_path_device_resident": {"mpix_s": 576000.0}, "roofline": {"frac": 0.97}, "serving": rates,
+            "alone_equal_oracle": "8/8", "oracle_check": "every served job", "server_stats": {"failed": 0}}
+    s = bench.serve_summary(line)
+    assert s["value"] == 57600.0 and s["served_vs_plain"] == 0.1 and s["h2d_link_frac"] == 0.97
+    assert [r["offered_jobs_s"] for r in s["rates"]] == [10.0, 100.0, 1000.0]
+    assert all(r["oracle_equal"] == "64/64" and r["same_as_alone"] == "64/64" for r in s["rates"])
+    assert "queue_p50_ms" not in s["rates"][0]
+    assert s["alone_equal_oracle"] == "8/8" and s["server_stats"]["failed"] == 0
+
+
+def test_default_line_folds_in_a_short_served_run():
+    args = bench.parse_args([])
+    assert args.workload == "stack6000x4000x7" and args.serve_pool > 0 and args.batch_count == 256
+    assert args.min_timed_s >= 0.5
