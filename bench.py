@@ -91,15 +91,15 @@ NCU_TRAFFIC = {
     ("k_pyramid", "stack4000x3000x3"): {"bytes": 116647680, "sources_sha256": "51d50f00dfb4fe6bf0b3fbd829edfbd37d05433985f0057cd6a55eace28f9b84"},
     ("k_apply_shifts", "apply6000x4000x7"): {"bytes": 955071744, "sources_sha256": "e265c02bbfa6e0cda0bd4c35ae4a6118438da478c9b3a3a35471b1d9ce84ba18"},
     # the 6000x4000x7 stack, `bench.py --profile --steps 2 --warmup 2` under
-    # ncu, mean over the captured launches: k_pyramid 531.93 MB read + 168.21 MB
-    # written (4 launches), k_bitmaps 224.68 + 6.10 MB (4), k_search_staged
-    # 56.39 + 0.00 MB (2), k_search_items 56.33 + 0.00 MB (2). Written bytes
+    # ncu, mean over the captured launches: k_pyramid 531.86 MB read + 168.06 MB
+    # written (4 launches), k_bitmaps 224.73 + 5.79 MB (4), k_search_staged
+    # 56.38 + 0.00 MB (2), k_search_items 56.33 + 0.00 MB (2). Written bytes
     # still dirty in L2 when a launch ends are not counted, hence writes below
     # the algorithmic figure
-    ("k_pyramid", "stack6000x4000x7"): {"bytes": 700147456, "sources_sha256": "856cea7dbe38c6a591a7eafbc97ec769bdeafc4bd91f0f909a33d8b081f93d69"},
-    ("k_bitmaps", "stack6000x4000x7"): {"bytes": 230780160, "sources_sha256": "8e622c45ee8187ebb5e305a16cbb099fe291ebf67c2c79a842239fe2687cdbc5"},
-    ("k_search_staged", "stack6000x4000x7"): {"bytes": 56387328, "sources_sha256": "10b4b42365bb6caae55dadf41a818eb9874fc888ce2b5f87bcba43e3b5b5e11a"},
-    ("k_search_items", "stack6000x4000x7"): {"bytes": 56330624, "sources_sha256": "1e55b420bbcedda9288d84af10bf5b197aed4561a7a34e42e68472d67fac3ac3"},
+    ("k_pyramid", "stack6000x4000x7"): {"bytes": 699921664, "sources_sha256": "05c99d248177ca13fecc586c0b584e768a7905956a261b2f4019a54686f47c17"},
+    ("k_bitmaps", "stack6000x4000x7"): {"bytes": 230528832, "sources_sha256": "93c617e24e66bcec772aa1f012ed0bed6cfdfd28c5bd3fd6a1d5a04c15920634"},
+    ("k_search_staged", "stack6000x4000x7"): {"bytes": 56384640, "sources_sha256": "370439610f1f1c12706f9c510e9d8b31872879be9448a85d34844dc31c9adb56"},
+    ("k_search_items", "stack6000x4000x7"): {"bytes": 56329856, "sources_sha256": "178915f00529fb7ac0a627038292eda2fcefa5a468a415e9cfbd054a949c4dac"},
 }
 
 

@@ -33,6 +33,9 @@ namespace {
 // (its coarse levels) are finished first.
 // 5 CTAs per SM (48 registers, no spills): 17.0 us for the 4000x3000x3 planes
 // and 59.9 us for 6000x4000x7, against 18.9 and 70.4 us at 4 (54 registers).
+// kChunk: the words a CTA packs (bit_chunk_words), a compile-time constant so
+// that the chunk arithmetic folds (as a kernel argument it cost ~1 us a pass).
+template <int kChunk>
 __global__ void __launch_bounds__(kBitThreads, 5)
 k_bitmaps(const mtb_layout_t L, uint8_t *__restrict__ ws, int tol, int deep_ctas) {
     __shared__ uint32_t s_hist[256];
@@ -53,27 +56,32 @@ k_bitmaps(const mtb_layout_t L, uint8_t *__restrict__ ws, int tol, int deep_ctas
     int item = blockIdx.x - deep_ctas;
     int l = L.tile_levels - 1;
     for (; l > 0; --l) {
-        const int per_level = bitmap_chunks(L, l, kBitWordsPerCta) * L.n;
+        const int per_level = bitmap_chunks(L, l, kChunk) * L.n;
         if (item < per_level) break;
         item -= per_level;
     }
-    const int ch = bitmap_chunks(L, l, kBitWordsPerCta);
+    const int ch = bitmap_chunks(L, l, kChunk);
     const int e = item / ch;
-    bitmap_chunk(L, ws, tol, e, l, item - e * ch, kBitWordsPerCta, &s_med);
+    bitmap_chunk(L, ws, tol, e, l, item - e * ch, kChunk, &s_med);
 }
 
 }  // namespace
 
 cudaError_t launch_bitmaps(const mtb_layout_t &L, int noise_tol, uint8_t *ws, cudaStream_t s, bool chained) {
+    const int cw = bit_chunk_words(L);
     long long per_exp = 0;
     for (int l = 0; l < L.tile_levels; ++l) {
         const long long words = (long long)L.bits_pitch[l] * L.height[l];
-        per_exp += (words + kBitWordsPerCta - 1) / kBitWordsPerCta;
+        per_exp += (words + cw - 1) / cw;
     }
     const int deep = L.levels > L.tile_levels ? L.n : 0;
     const long long grid = deep + per_exp * L.n;
     if (grid > 0x7fffffffLL) return cudaErrorInvalidValue;
-    return launch_k(k_bitmaps, dim3((unsigned)grid), dim3(kBitThreads), s, chained, L, ws, noise_tol, deep);
+    if (cw == 2 * kBitWordsPerCta)
+        return launch_k(k_bitmaps<2 * kBitWordsPerCta>, dim3((unsigned)grid), dim3(kBitThreads), s, chained, L, ws,
+                        noise_tol, deep);
+    return launch_k(k_bitmaps<kBitWordsPerCta>, dim3((unsigned)grid), dim3(kBitThreads), s, chained, L, ws, noise_tol,
+                    deep);
 }
 
 }  // namespace mtb

@@ -97,7 +97,7 @@ __host__ __device__ __forceinline__ int search_counter_words(const mtb_layout_t 
 
 // Bitmap chunks of tile level l of one exposure, and the value of bit_done[e][l]
 // once level l of an exposure is complete (deep levels are built whole).
-// (chunk_words: words per bitmap chunk, kBitWordsPerCta for the stage kernel)
+// (chunk_words: words per bitmap chunk, bit_chunk_words(L) for the stage kernel)
 __host__ __device__ __forceinline__ int bitmap_chunks(const mtb_layout_t &L, int l, int chunk_words) {
     return (L.bits_pitch[l] * L.height[l] + chunk_words - 1) / chunk_words;
 }

@@ -28,9 +28,17 @@ constexpr int kGroupsPerRow = kTileCols / 16 + 1;  // 16-pixel groups touching o
 // one (exposure, level) plane into bits.
 constexpr int kBitThreads = 256;
 // 2048: about one wave of 5 CTAs per SM on the 4000x3000x3 planes (one-call
-// step 80.7 -> 80.0 us against 1024; 512: 84.4 us; 4096: 81.5 us, though
-// 6000x4000x7 prefers 4096: 248 against 251 us).
+// step 80.7 -> 80.0 us against 1024; 512: 84.4 us; 4096: 81.5 us).
 constexpr int kBitWordsPerCta = 2048;
+
+// Words one bitmap CTA packs on a stack: twice kBitWordsPerCta once level 0 of
+// all exposures has 2^22 words or more, so that its chunks still fill a wave
+// (6000x4000x7, 5.3 M words: one-call step 242.9 -> 240.2 us; 4000x3000x3,
+// 1.1 M words, keeps 2048: 4096 took its bitmap stage from 17.6 to 18.6 us).
+__host__ __device__ inline int bit_chunk_words(const mtb_layout_t &L) {
+    const long long words0 = (long long)L.n * L.bits_pitch[0] * L.height[0];
+    return words0 >= (1ll << 22) ? 2 * kBitWordsPerCta : kBitWordsPerCta;
+}
 
 constexpr int kMaxShiftThreads = 256;
 

@@ -237,7 +237,7 @@ void plan_search(const mtb_layout_t &L, int ref_idx, long long cap, int32_t *shi
     P.level_shifts_out = level_shifts_out;
     P.timeout_ns = timeout_ns;
     P.withhold_pair = withhold_pair;
-    P.bit_chunk_words = kBitWordsPerCta;
+    P.bit_chunk_words = bit_chunk_words(L);
     P.window_items = 0;
     for (int l = L.levels - 1; l >= P.lc; --l) {
         const long long words = (long long)L.bits_pitch[l] * L.height[l];
@@ -374,7 +374,7 @@ int plan_staged_search(const mtb_layout_t &L, int ref_idx, int cluster, int clus
     P.level_shifts_out = level_shifts_out;
     P.timeout_ns = timeout_ns;
     P.withhold_pair = withhold_pair;
-    P.bit_chunk_words = kBitWordsPerCta;
+    P.bit_chunk_words = bit_chunk_words(L);
     P.status_out = nullptr;
     if (cluster < 1 || cluster > kStMaxCluster || clusters < 1 || P.pairs < 1) return MTB_ERR_INVALID_ARG;
     const int top = L.levels - 1;
